@@ -1,0 +1,181 @@
+"""Seeded synthetic inputs: solid masks, random populations and workload
+parameters for the Bingham LBM solver.
+
+This module holds input generators only (geometry, random numbers, the
+mapping of a requested Bingham number to a yield stress through the
+*continuum* closed forms of the flows).  It contains none of the lattice
+Boltzmann method's arithmetic; both the CUDA path and the CPU oracle receive
+what it produces.
+
+Geometry conventions (all masks are uint8, 1 = solid, shape (nz, ny, nx),
+x fastest):
+
+* plane channel (Sec. 4.3 geometry in 2D): row y = 0 solid, periodic in x and
+  y, so the single solid row is the wall on both sides and the channel has
+  ny - 1 fluid rows (odd ny - 1 puts a node on the centre line);
+* square duct (Sec. 4.3): rows y = 0 and z = 0 solid, periodic wrap, flow
+  along x; the fluid cross-section is (ny - 1) x (nz - 1);
+* porous medium: random sequential addition of non-overlapping spheres in a
+  periodic box (minimum-image distance), radius uniform in [r_min, r_max],
+  stopping once the voxel porosity (fraction of cells whose centre is outside
+  every sphere) reaches the target;
+* cylinder array (Sec. 4.5): one cylinder of diameter D in an L x L periodic
+  cell.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+
+def channel_mask(nx: int = 4, ny: int = 64) -> np.ndarray:
+    m = np.zeros((1, ny, nx), np.uint8)
+    m[0, 0, :] = 1
+    return m
+
+
+def duct_mask(nx: int, ny: int, nz: int) -> np.ndarray:
+    m = np.zeros((nz, ny, nx), np.uint8)
+    m[:, 0, :] = 1
+    m[0, :, :] = 1
+    return m
+
+
+def periodic_box_mask(nx: int, ny: int, nz: int) -> np.ndarray:
+    return np.zeros((nz, ny, nx), np.uint8)
+
+
+def cylinder_mask(L: int = 80, D: float = 32.0, shift: float = 0.0) -> np.ndarray:
+    """2D periodic cell with one cylinder; cell centres inside are solid."""
+    y, x = np.mgrid[0:L, 0:L].astype(np.float64)
+    c = (L - 1) / 2.0 + shift
+    inside = (x - c) ** 2 + (y - (L - 1) / 2.0) ** 2 <= (D / 2.0) ** 2
+    return inside.astype(np.uint8)[None, :, :]
+
+
+def porous_mask(n: int | tuple = 64, porosity: float = 0.7, r_min: float = 6.0,
+                r_max: float = 10.0, seed: int = 1, max_attempts: int = 10_000_000):
+    """Random non-overlapping spheres in a periodic box.
+
+    Returns (mask, info) with info = {"porosity", "spheres", "attempts",
+    "reached"}; `reached` is False if the attempt cap stopped the packing
+    before the target porosity (jamming).  Generator: numpy PCG64 seeded
+    with `seed`.
+    """
+    nx, ny, nz = (n, n, n) if isinstance(n, int) else n
+    rng = np.random.Generator(np.random.PCG64(seed))
+    mask = np.zeros((nz, ny, nx), np.uint8)
+    box = np.array([nx, ny, nz], np.float64)
+    centres = np.zeros((0, 3), np.float64)
+    radii = np.zeros(0, np.float64)
+    solid = 0
+    total = nx * ny * nz
+    target_solid = (1.0 - porosity) * total
+    attempts = 0
+    batch = 256
+    while solid < target_solid and attempts < max_attempts:
+        cand = rng.random((batch, 3)) * box
+        rad = r_min + (r_max - r_min) * rng.random(batch)
+        for k in range(batch):
+            attempts += 1
+            if len(radii):
+                d = centres - cand[k]
+                d -= box * np.round(d / box)
+                dist = np.sqrt(np.sum(d * d, axis=1))
+                if np.any(dist < radii + rad[k]):
+                    continue
+            centres = np.vstack([centres, cand[k]])
+            radii = np.append(radii, rad[k])
+            solid += _paint_sphere(mask, cand[k], rad[k])
+            if solid >= target_solid:
+                break
+    info = {"porosity": 1.0 - mask.sum() / total, "spheres": int(len(radii)),
+            "attempts": attempts, "reached": bool(solid >= target_solid)}
+    return mask, info
+
+
+def _paint_sphere(mask, c, r):
+    nz, ny, nx = mask.shape
+    lo = np.floor(c - r).astype(int)
+    hi = np.ceil(c + r).astype(int)
+    xs = np.arange(lo[0], hi[0] + 1)
+    ys = np.arange(lo[1], hi[1] + 1)
+    zs = np.arange(lo[2], hi[2] + 1)
+    Z, Y, X = np.meshgrid(zs, ys, xs, indexing="ij")
+    inside = (X - c[0]) ** 2 + (Y - c[1]) ** 2 + (Z - c[2]) ** 2 <= r * r
+    zi, yi, xi = Z[inside] % nz, Y[inside] % ny, X[inside] % nx
+    before = int(mask[zi, yi, xi].sum())
+    mask[zi, yi, xi] = 1
+    return int(inside.sum()) - before
+
+
+def random_populations(weights: np.ndarray, ncells: int, amplitude: float = 0.05,
+                       seed: int = 0) -> np.ndarray:
+    """f[i, n] = w_i (1 + amplitude * r), r uniform in [-1, 1): a seeded
+    perturbation of the rest state.  `weights` is passed in by the caller."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    r = rng.uniform(-1.0, 1.0, size=(len(weights), ncells))
+    return np.asarray(weights, np.float64)[:, None] * (1.0 + amplitude * r)
+
+
+def permutation(c_from: np.ndarray, c_to: np.ndarray) -> np.ndarray:
+    """Index map p with c_to[p[k]] == c_from[k]: population k of one velocity
+    order sits at p[k] in the other."""
+    lookup = {tuple(int(v) for v in c): k for k, c in enumerate(c_to)}
+    return np.array([lookup[tuple(int(v) for v in c)] for c in c_from], np.int64)
+
+
+# --- workload parameters ---------------------------------------------------
+
+def channel_bn_to_xi(bn: float) -> float:
+    """Plane Bingham-Poiseuille flow: invert Bn = sigma_y H / (mu_p U_mean)
+    for xi = y_0 / h, using U_mean = (g h^2 / 3 nu)(1 - 3 xi/2 + xi^3/2) and
+    sigma_y = xi rho g h, which give Bn = 6 xi / (1 - 1.5 xi + 0.5 xi^3)."""
+    lo, hi = 0.0, 1.0
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        val = 6.0 * mid / (1.0 - 1.5 * mid + 0.5 * mid ** 3)
+        if val < bn:
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)
+
+
+def channel_params(H: int = 63, nu_p: float = 0.1, u_newton: float = 0.01, bn: float = 1.0):
+    """Body force for a Newtonian centre-line speed u_newton and the yield
+    stress for the requested Bingham number (rho = 1)."""
+    h = H / 2.0
+    g = 2.0 * nu_p * u_newton / (h * h)
+    xi = channel_bn_to_xi(bn) if bn > 0 else 0.0
+    return {"g": g, "sigma_y": xi * g * h, "xi": xi, "h": h, "nu_p": nu_p}
+
+
+BI_CR = 4.0 / (2.0 + math.sqrt(math.pi))
+C_MAX = 1.178741652
+
+
+def duct_bn_to_bi(bn: float) -> float:
+    """Square duct: map an a-posteriori Bn = sigma_y H / (mu_p U_max) to the
+    a-priori Bi = 4 sigma_y / (rho g H) through the Mosolov-Miasnikov form
+    U_max = g c_max H^2 / (16 mu_p) (1 - Bi/Bi_cr)^2 (eq. U_max_square;
+    about 2 % off for Bi > 0, which only shifts the realised Bn)."""
+    # Bn = (Bi g H^2 / 4) / (g c_max H^2 / 16 (1 - Bi/Bi_cr)^2) = 4 Bi / (c_max (1 - Bi/Bi_cr)^2)
+    lo, hi = 0.0, BI_CR * (1 - 1e-12)
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        val = 4.0 * mid / (C_MAX * (1.0 - mid / BI_CR) ** 2)
+        if val < bn:
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)
+
+
+def duct_params(H: int = 127, nu_p: float = 0.1, u_newton: float = 0.02, bn: float = 2.0):
+    """Body force for a Newtonian centre-line speed u_newton in a square duct of
+    side H, and the yield stress for the requested Bn (rho = 1)."""
+    g = 16.0 * nu_p * u_newton / (C_MAX * H * H)
+    bi = duct_bn_to_bi(bn) if bn > 0 else 0.0
+    return {"g": g, "sigma_y": bi * g * H / 4.0, "bi": bi, "nu_p": nu_p}
