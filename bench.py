@@ -1,0 +1,397 @@
+"""Throughput benchmark of the fused Bingham LBM step on GB300.
+
+Workload: 3D square duct, D3Q27, 256 (x, streamwise, periodic) x 128 x 128
+cells with solid rows y = 0 and z = 0 (127 x 127 fluid cross-section,
+4,129,024 fluid cells), body force along x, Bn = 2 (a-posteriori, mapped to
+the yield stress through the Mosolov-Miasnikov duct formula), nu_p = 0.1,
+FP32 population storage, started from rest.  One bench "step" is one lattice
+time step of BOTH Bingham models on their own copy of the duct (PR with
+m = 1e6 and IR), so both fused kernels and the check-step reductions (every
+100 steps) are exercised.  The metric is MLUPS: fluid-cell updates per second.
+
+Timing: W untimed warm-up steps, then K timed steps bracketed by a barrier and
+cudaDeviceSynchronize, measured with CUDA events on the solvers' stream (the
+IR phase and the PR phase each have their own events, which gives each
+kernel's average launch duration).  The populations (2 x 905 MB) are far
+larger than L2, so no flush is needed between steps.
+
+--impl reference times the FP64 CPU oracle (the correctness reference) on
+the host cores, on a bounded sample of the same duct, one sample per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "D3Q27 Bingham MLUPS and % HBM roofline; served solves/s, p50/p99 latency"
+NX, NY, NZ = 256, 128, 128
+LATTICE = "D3Q27"
+NU_P = 0.1
+BN = 2.0
+M_PR = 1e6
+CHECK_EVERY = 100
+SAMPLE_NX = 4          # x-extent of the oracle's sample of the duct (periodic along x)
+
+
+def workload_params():
+    from paper_1610_01388_gb300 import workloads as W
+    prm = W.duct_params(H=NY - 1, nu_p=NU_P, u_newton=0.02, bn=BN)
+    return prm["g"], prm["sigma_y"]
+
+
+def workload_config(extra=None):
+    cfg = {"workload": f"square duct {LATTICE} {NX}x{NY}x{NZ} ({NY - 1}x{NZ - 1} fluid "
+                       "cross-section), "
+                       f"PR (m={M_PR:g}) + IR per step, Bn={BN:g}, nu_p={NU_P}, FP32 populations, "
+                       f"check step every {CHECK_EVERY}",
+           "lattice": LATTICE, "nx": NX, "ny": NY, "nz": NZ, "models": ["PR", "IR"],
+           "storage": "F32", "l2": "inputs larger than L2 (2 x 905 MB populations per model)"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+def measured_hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# --- distributed plumbing -----------------------------------------------------
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def reduce_max(value, backend_device=None):
+    """Max of a float over ranks (identity without a process group)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64,
+                     device=backend_device if backend_device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+def aggregate(updates_per_rank, max_seconds, world_size):
+    """Whole-job MLUPS: every rank processes the same number of updates."""
+    return updates_per_rank * world_size / max_seconds / 1e6
+
+
+# --- clocks --------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", str(self.dev)], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    rows.append(parts)
+                except Exception:
+                    pass
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = []
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        smax = None
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax = float(r[2])
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if r[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --- our arm ----------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_1610_01388_gb300 import _build, lbm
+    from paper_1610_01388_gb300 import workloads as W
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1 and not dist.is_initialized():
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if not os.path.exists(lbm.LIB_PATH):
+        _build.build()
+    dev = torch.device("cuda", local)
+    g, sy = workload_params()
+    mask = W.duct_mask(NX, NY, NZ)
+    nfluid = int((mask == 0).sum())
+
+    solvers = {}
+    for model in ("IR", "PR"):
+        solvers[model] = lbm.Solver(LATTICE, mask, model=model, storage="F32", mu_p=NU_P,
+                                    sigma_y=sy, m=M_PR, g=(g, 0.0, 0.0),
+                                    check_every=CHECK_EVERY, use_torch=True)
+    stream = torch.cuda.current_stream(dev)
+
+    # warm-up (also captures the CUDA graphs)
+    for model in ("IR", "PR"):
+        solvers[model].step(args.warmup)
+    torch.cuda.synchronize(dev)
+
+    K = args.steps
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    ev[0].record(stream)
+    solvers["IR"].step(K)
+    ev[1].record(stream)
+    solvers["PR"].step(K)
+    ev[2].record(stream)
+    torch.cuda.synchronize(dev)
+    t1 = time.perf_counter()
+    barrier()
+    clk = clocks.stop()
+    ms_ir = ev[0].elapsed_time(ev[1])
+    ms_pr = ev[1].elapsed_time(ev[2])
+    ms_total = ms_ir + ms_pr
+    max_s = reduce_max(ms_total / 1e3, dev if ws > 1 else None)
+    value = aggregate(2.0 * nfluid * K, max_s, ws)
+
+    # residual sanity (the run must stay finite)
+    for model in ("IR", "PR"):
+        solvers[model].residual()
+
+    info_ir = solvers["IR"].info
+    info_pr = solvers["PR"].info
+    peak, peak_kind = measured_hbm_peak()
+    launches_per_model = K + K // CHECK_EVERY   # step kernels + check-step finalisers
+    per = {}
+    for model, ms, inf in (("IR", ms_ir, info_ir), ("PR", ms_pr, info_pr)):
+        t_launch = ms / 1e3 / K
+        gbs = inf.bytes_per_fluid_update * nfluid / t_launch / 1e9
+        per[model] = {"bytes_per_update": inf.bytes_per_fluid_update, "launch_us": t_launch * 1e6,
+                      "achieved_gbs": gbs, "frac": gbs / peak,
+                      "mlups": nfluid / t_launch / 1e6}
+    dom = "PR" if ms_pr >= ms_ir else "IR"
+    roof = {"bound": "hbm", "kernel": f"k_step<{LATTICE},{dom},float> (dominant by time)",
+            "achieved": round(per[dom]["achieved_gbs"], 1), "peak": peak,
+            "peak_kind": f"{peak_kind} (copy bandwidth)", "unit": "GB/s",
+            "frac": round(per[dom]["frac"], 4),
+            "bytes_per_fluid_update": per[dom]["bytes_per_update"],
+            "fluid_cells_per_launch": nfluid,
+            "traffic": args.traffic,
+            "per_model": {k: {kk: round(vv, 4) if isinstance(vv, float) else vv
+                              for kk, vv in v.items()} for k, v in per.items()}}
+    for s in solvers.values():
+        s.close()
+    del solvers
+    torch.cuda.synchronize(dev)
+
+    e2e = run_e2e(args, mask, nfluid, g, sy, dev)
+    cpu = run_cpu_baseline(args) if (rank == 0 and ws == 1 and not args.no_cpu) else None
+    if rank == 0:
+        line = {"metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": ws,
+                "steps": K, "warmup": args.warmup, "ms_per_step": round(max_s * 1e3 / K, 5),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic",
+                "config": workload_config({"per_rank": "independent duct pair per GPU",
+                                           "fluid_cells": nfluid}),
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": 2 * launches_per_model, "clocks": clk,
+                "wall_s_timed_region": round(t1 - t0, 4)}
+        print(json.dumps(line), flush=True)
+    if ws > 1 and dist.is_initialized():
+        dist.destroy_process_group()
+
+
+def run_e2e(args, mask, nfluid, g, sy, dev):
+    """The same metric through the public C ABI with host buffers: per model a
+    solve = lbm_create from the host mask (H2D), lbm_step(K), lbm_fields to
+    host (D2H of rho and u), lbm_destroy; all inside the timed region."""
+    import torch
+    from paper_1610_01388_gb300 import lbm
+    K = args.e2e_steps if args.e2e_steps > 0 else args.steps
+    rho = np.empty(mask.size)
+    u = np.empty((3, mask.size))
+    torch.cuda.synchronize(dev)
+    barrier()
+    t0 = time.perf_counter()
+    for model in ("IR", "PR"):
+        p = lbm.lbm_params_default(model=model, storage="F32", mu_p=NU_P, sigma_y=sy, m=M_PR,
+                                   g=(g, 0.0, 0.0), check_every=CHECK_EVERY)
+        h = lbm.lbm_create(LATTICE, mask, p)
+        lbm.lbm_step(h, K)
+        lib = lbm.library()
+        import ctypes
+        vp = ctypes.c_void_p
+        lbm._check(lib.lbm_fields(h, vp(rho.ctypes.data), vp(u[0].ctypes.data),
+                                  vp(u[1].ctypes.data), vp(u[2].ctypes.data)))
+        lbm.lbm_destroy(h)
+    t1 = time.perf_counter()
+    ws, _, _ = dist_env()
+    max_s = reduce_max(t1 - t0, dev if ws > 1 else None)
+    return {"value": round(aggregate(2.0 * nfluid * K, max_s, ws), 1), "unit": "MLUPS",
+            "h2d_bytes_per_step": round(2 * mask.size / K, 3),
+            "d2h_bytes_per_step": round(2 * 4 * 8 * mask.size / K, 3),
+            "steps": K, "what": "per model: lbm_create (host mask H2D) + lbm_step(K) + "
+                                "lbm_fields (rho,u D2H) + lbm_destroy, inside the timed region"}
+
+
+# --- oracle arms ------------------------------------------------------------------
+
+def _oracle_sample_step(states):
+    for st in states:
+        st.step(1)
+
+
+def _oracle_states():
+    import oracle
+    from paper_1610_01388_gb300 import workloads as W
+    g, sy = workload_params()
+    mask = W.duct_mask(SAMPLE_NX, NY, NZ)
+    states = []
+    for model in ("IR", "PR"):
+        p = oracle.params(model=model, nu_p=NU_P, sigma_y=sy, m=M_PR, g=(g, 0, 0))
+        states.append(oracle.State(LATTICE, p, mask, nthreads=0))
+    return states, int((mask == 0).sum())
+
+
+def run_cpu_baseline(args):
+    """The oracle as it stands on the host cores: a bounded sample (a
+    4-cell-long slab of the same duct, both models, periodic along x) stepped
+    for about args.cpu_seconds seconds."""
+    import oracle
+    states, nf = _oracle_states()
+    _oracle_sample_step(states)
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        _oracle_sample_step(states)
+        n += 1
+        if time.perf_counter() - t0 > args.cpu_seconds:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": round(2.0 * nf * n / dt / 1e6, 4), "unit": "MLUPS",
+            "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{SAMPLE_NX}x{NY}x{NZ} slab of the duct (both models, {nf} fluid cells "
+                      f"each), {n} steps in {dt:.1f} s, FP64"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    states, nf = _oracle_states()
+    for _ in range(args.warmup):
+        _oracle_sample_step(states)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        _oracle_sample_step(states)
+    dt = time.perf_counter() - t0
+    value = 2.0 * nf * args.steps / dt / 1e6
+    line = {"metric": METRIC, "value": round(value, 4), "unit": "MLUPS", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(dt * 1e3 / args.steps, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": workload_config({"sample": f"{SAMPLE_NX}x{NY}x{NZ} slab per step"}),
+            "cpu_baseline": {"value": round(value, 4), "unit": "MLUPS",
+                             "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": f"{SAMPLE_NX}x{NY}x{NZ} slab of the duct, both models, "
+                                       "one time step each per bench step"},
+            "e2e": {"value": round(value, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=100)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--e2e-steps", type=int, default=0)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="ncu dram bytes per launch of the dominant kernel, if captured")
+    ap.add_argument("--ny", type=int, default=NY, help="duct cross-section (profiling runs)")
+    ap.add_argument("--nz", type=int, default=NZ)
+    args = ap.parse_args(argv)
+    global NY, NZ
+    NY, NZ = args.ny, args.nz
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,197 @@
+/*
+ * bingham_lbm.h -- C ABI of the GB300 (sm_103a) lattice Boltzmann solver for
+ * Bingham fluids.
+ *
+ * The method is the one of Regulski, Leonardi & Szumbarski, "On the spatial
+ * convergence and transient behaviour of lattice Boltzmann methods for
+ * modelling fluids with yield stress" (arXiv:1610.01388):
+ *
+ *   PR  Papanastasiou-regularised model (Sec. 3.1): strain rate from the
+ *       non-equilibrium second moment with the previous step's relaxation
+ *       time (eq. LBM_strain_rate), apparent viscosity eq. (Pap_reg_1) with the
+ *       zero-strain cut-off eq. (PR_interpolation), relaxation time eq.
+ *       (tau_visc), TRT collision with magic number Lambda (Sec. 2.1) and
+ *       exact-difference forcing eq. (14);
+ *   IR  locally implicit model (Secs. 2.3, 3.2): T = sum c c (f - f_eq), the
+ *       closed-form Bingham solution of eq. (Vikh_main_short) given by eqs.
+ *       (Vikh_sigmaS_formula)/(Vikh_sigmaS_tensor), post-collision populations
+ *       eq. (Vikh_postCol) with f^sigma of eq. (Vikh_f_stress) and the force
+ *       term of eq. (Vikh_force).
+ *
+ * Both run on D2Q9, D3Q15, D3Q19 and D3Q27 (Sec. 4.1), with streaming eq. (8)
+ * in pull form, halfway bounce-back on solid cells (Sec. 4.3) and periodic
+ * wrap at the domain faces.  Where the printed paper is garbled the library
+ * takes these readings: the cut-off interpolation divides by gdot^C; IR yields
+ * where |T| >= sqrt(2) sigma_y; f^sigma_i = w_i/(2 c_s^4)(c_i c_i - c_s^2 I):A
+ * with A = -sigma_bar + s/2 and sigma_bar = sigma - (tr sigma / d) I; the IR
+ * force term is Phi_i = w_i (c_i . F)/c_s^2 with F = rho g and the velocity
+ * u = (j + F/2)/rho.
+ *
+ * Conventions for every call:
+ *   - Grid: nx * ny * nz cells, x fastest: cell = x + nx * (y + ny * z).
+ *     D2Q9 requires nz == 1.  At most 2^31 - 1 cells.
+ *   - Populations at the ABI are FULL distribution values f_i (not offsets),
+ *     FP64, laid out f[i * N + cell], in the library's velocity order, which
+ *     lbm_lattice_info() reports.  This is the post-collision state after the
+ *     last completed step (what the next step streams from).
+ *   - Macroscopic fields are the moments of the streamed (pre-collision)
+ *     populations of the next step: rho and u_real = (j + F/2)/rho (Sec. 2.4).
+ *     Solid cells report rho = 0, u = 0.
+ *   - Ownership: the library owns the solver handle and, for lbm_create, all
+ *     device memory it allocates.  Every host pointer argument is owned by the
+ *     caller and only read/written during the call.  The solid mask is copied.
+ *   - Streams: work is enqueued on the CUDA stream given at creation (NULL =
+ *     the legacy default stream).  lbm_step is asynchronous; calls that return
+ *     host data synchronise that stream.
+ *   - Errors: every call returns an lbm_status; on failure lbm_last_error()
+ *     returns a thread-local message.  After a CUDA error the handle is
+ *     poisoned: every later call on it returns LBM_ECUDA until lbm_destroy.
+ *     No call throws, aborts or exits.
+ */
+#ifndef BINGHAM_LBM_H
+#define BINGHAM_LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_API_VERSION 1
+
+typedef struct lbm_solver lbm_solver; /* opaque, library-owned */
+
+typedef enum { LBM_D2Q9 = 0, LBM_D3Q15 = 1, LBM_D3Q19 = 2, LBM_D3Q27 = 3 } lbm_lattice;
+
+typedef enum { LBM_MODEL_PR = 0, LBM_MODEL_IR = 1 } lbm_model;
+
+/* Population storage in device memory.  Every form stores the offset
+ * f_i - w_i from the rest state; the collision arithmetic is FP64 for
+ * LBM_F64 and FP32 for the others. */
+typedef enum {
+    LBM_F64 = 0,      /* double offsets */
+    LBM_F32 = 1,      /* float offsets */
+    LBM_F16_OFS = 2,  /* half offsets, scaled */
+    LBM_BF16_OFS = 3  /* bfloat16 offsets, scaled */
+} lbm_storage;
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_EINVAL = 1,       /* invalid argument; nothing was changed */
+    LBM_ENOMEM = 2,       /* device or host allocation failed */
+    LBM_ECUDA = 3,        /* CUDA runtime error; the handle is poisoned */
+    LBM_ENONFINITE = 4,   /* a check step found a non-finite density */
+    LBM_ETIMEOUT = 5,     /* a bounded device wait ran out */
+    LBM_EBUSY = 6,        /* resource in use */
+    LBM_EUNSUPPORTED = 7  /* combination not built into this library */
+} lbm_status;
+
+/* Flags (lbm_params.flags). */
+#define LBM_FLAG_BURNETT_X 0x1u /* zero the xx components of D (PR) and of T (IR),
+                                   the Burnett-suppressed variant of Secs. 4.2.1-4.2.2
+                                   for flow along x */
+
+/* Rheology, forcing and run-control parameters (lattice units, rho_0 = 1). */
+typedef struct {
+    int32_t model;       /* lbm_model */
+    int32_t storage;     /* lbm_storage */
+    double mu_p;         /* plastic viscosity; nu_p = mu_p / rho_0; > 0 */
+    double sigma_y;      /* yield stress; >= 0 */
+    double m;            /* Papanastasiou parameter (PR); >= 0 */
+    double gammadot_c;   /* PR zero-strain cut-off gdot^C (Sec. 3.1); > 0; default 1e-8 */
+    double g[3];         /* body acceleration; force density F = rho g; g[2] = 0 for D2Q9 */
+    double magic;        /* TRT magic number Lambda (PR), > 0; default 0.25 (Sec. 2.1) */
+    int32_t check_every; /* every k-th step also computes the flow rate and the
+                            residual (0 = never) */
+    uint32_t flags;      /* LBM_FLAG_* */
+} lbm_params;
+
+/* Fills *p with defaults: IR, F32, mu_p 0.1, sigma_y 0, m 0, gammadot_c 1e-8,
+ * g 0, magic 0.25, check_every 0, flags 0. */
+lbm_status lbm_params_default(lbm_params *p);
+
+/* Velocity set of a lattice in the library's order: Q, D, c[Q][3] (int),
+ * w[Q] (double).  Any output pointer may be NULL.  Host only. */
+lbm_status lbm_lattice_info(lbm_lattice lat, int *Q, int *D, int *c, double *w);
+
+/* Device bytes lbm_create_with_workspace needs for this problem (populations
+ * A/B, link masks, PR tau A/B, residual snapshot, reduction partials). */
+lbm_status lbm_workspace_bytes(lbm_lattice lat, int nx, int ny, int nz,
+                               const lbm_params *p, size_t *bytes);
+
+/* Creates a solver at rest (f_i = w_i, rho = 1, u = 0; PR tau = 1/2 + 3 nu_0,
+ * nu_0 = nu_p + m sigma_y).  solid_mask: host, nx*ny*nz bytes, nonzero =
+ * solid, copied.  At least one cell must be fluid.  cuda_stream: a
+ * cudaStream_t or NULL.  The library allocates its device memory. */
+lbm_status lbm_create(lbm_solver **out, lbm_lattice lat, int nx, int ny, int nz,
+                      const uint8_t *solid_mask, const lbm_params *p, void *cuda_stream);
+
+/* As lbm_create, but the caller provides the device memory: workspace must be
+ * a device pointer, 256-byte aligned, of at least lbm_workspace_bytes() bytes,
+ * and stay valid until lbm_destroy (e.g. a torch tensor kept alive). */
+lbm_status lbm_create_with_workspace(lbm_solver **out, lbm_lattice lat, int nx, int ny,
+                                     int nz, const uint8_t *solid_mask, const lbm_params *p,
+                                     void *cuda_stream, void *workspace, size_t workspace_bytes);
+
+/* Advances nsteps >= 0 time steps (one fused stream+collide launch each;
+ * long runs are replayed through captured CUDA graphs).  Asynchronous. */
+lbm_status lbm_step(lbm_solver *s, int64_t nsteps);
+
+/* Waits for all work enqueued on the solver's stream. */
+lbm_status lbm_sync(lbm_solver *s);
+
+/* Copies rho and u_real of every cell to host arrays of N doubles each; any
+ * pointer may be NULL.  Synchronises. */
+lbm_status lbm_fields(lbm_solver *s, double *rho, double *ux, double *uy, double *uz);
+
+/* Same fields into device arrays (N doubles each, may be NULL); asynchronous. */
+lbm_status lbm_fields_device(lbm_solver *s, double *rho, double *ux, double *uy, double *uz);
+
+/* Flow rate along axis a (0 = x, 1 = y, 2 = z): Q_a = (1/L_a) sum over fluid
+ * cells of u_real,a, the volumetric flow through one cross-section
+ * (Sec. 4.5: U_avg = Q / L^2).  FP64 accumulation in a fixed order.
+ * Synchronises. */
+lbm_status lbm_flowrate(lbm_solver *s, int axis, double *q);
+
+/* Totals of the current state over fluid cells: mass sum f_i and momentum
+ * sum c_i f_i (FP64 accumulation, fixed order).  Synchronises. */
+lbm_status lbm_totals(lbm_solver *s, double *mass, double momentum[3]);
+
+/* Result of the last check step (check_every > 0): residual
+ * sqrt(sum |u - u_prev|^2 / sum |u|^2) against the previous check step
+ * (-1 before two check steps), its step index, and the flow rate along x at
+ * that step.  Returns LBM_ENONFINITE if that check step saw a non-finite
+ * density.  Synchronises. */
+lbm_status lbm_residual(lbm_solver *s, double *residual, int64_t *at_step, double *flow_x);
+
+/* Replace / read the population state (host, FP64 full f, Q*N, library
+ * order).  Synchronises. */
+lbm_status lbm_set_populations(lbm_solver *s, const double *f);
+lbm_status lbm_get_populations(lbm_solver *s, double *f);
+
+/* PR relaxation-time field (host, N doubles).  LBM_EINVAL for IR. */
+lbm_status lbm_set_tau(lbm_solver *s, const double *tau);
+lbm_status lbm_get_tau(lbm_solver *s, double *tau);
+
+/* Problem description of a live solver. */
+typedef struct {
+    int32_t lattice, Q, D, nx, ny, nz;
+    int64_t cells, fluid_cells, steps_done;
+    int32_t model, storage;
+    double bytes_per_fluid_update; /* algorithmic HBM bytes of one fluid-cell update */
+    size_t device_bytes;
+} lbm_info;
+lbm_status lbm_get_info(const lbm_solver *s, lbm_info *info);
+
+/* Releases the handle and the device memory the library allocated. */
+void lbm_destroy(lbm_solver *s);
+
+/* Thread-local message of the last failing call on this thread. */
+const char *lbm_last_error(void);
+const char *lbm_status_string(lbm_status st);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BINGHAM_LBM_H */

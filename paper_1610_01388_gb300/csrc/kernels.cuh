@@ -1,0 +1,643 @@
+// Fused pull stream-and-collide kernels for the PR and IR Bingham models.
+//
+// One thread owns one cell.  Per fluid cell and time step it
+//   1. gathers the Q incoming populations (eq. 8, pull form): population i
+//      comes from the cell at x - c_i (periodic wrap) or, when that cell is
+//      solid, is the cell's own outgoing population in the opposite direction
+//      (halfway bounce-back, Sec. 4.3);
+//   2. forms the moments rho, j, Pi (eq. MomentsLBM) in registers;
+//   3. collides:
+//      PR  T = Pi - rho c_s^2 I - rho u u, D = -T/(2 tau_old c_s^2)
+//          (eq. LBM_strain_rate), gdot = sqrt(2 D:D), nu_app from eqs.
+//          (Pap_reg_1)/(PR_interpolation), tau = 1/2 + nu_app/c_s^2
+//          (eq. tau_visc), TRT with tau_odd from Lambda (Sec. 2.1) and the
+//          exact-difference force of eq. (14);
+//      IR  u = (j + F/2)/rho, T as above, the closed-form solution of
+//          eq. (Vikh_main_short) (eqs. Vikh_sigmaS_formula/tensor, yield where
+//          |T| >= sqrt2 sigma_y), A = -sigma_bar + s/2, and the post-collision
+//          populations f_eq + w/(2 c_s^4)(cc - c_s^2 I):A + Phi/2 of
+//          eqs. (Vikh_postCol)/(Vikh_f_stress)/(Vikh_force);
+//   4. stores the Q outgoing populations (and, PR, the new tau in place).
+//
+// Populations are stored as offsets f_i - w_i from the rest state, so every
+// moment is formed from small numbers (no cancellation against the weights).
+// On check steps the same launch also accumulates the flow-rate sums and the
+// residual against the previous snapshot into per-block FP64 partials.
+#pragma once
+
+#include <cstdint>
+#include <type_traits>
+#include <utility>
+
+#include <cuda_runtime.h>
+
+#include "../../include/bingham_lbm.h"
+#include "lattice.cuh"
+#include "lbm_internal.h"
+
+namespace blbm {
+
+// ---------------------------------------------------------------------------
+// compile-time loop
+template <int I, int N, class F>
+__device__ __forceinline__ void static_for(F&& f) {
+    if constexpr (I < N) {
+        f(std::integral_constant<int, I>{});
+        static_for<I + 1, N>(std::forward<F>(f));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// storage
+template <class S> struct Store;
+template <> struct Store<float> {
+    using R = float;
+    static __device__ __forceinline__ R ld(const float* p) { return __ldg(p); }
+    static __device__ __forceinline__ void st(float* p, R v) { *p = v; }
+};
+template <> struct Store<double> {
+    using R = double;
+    static __device__ __forceinline__ R ld(const double* p) { return __ldg(p); }
+    static __device__ __forceinline__ void st(double* p, R v) { *p = v; }
+};
+
+// Rheology constants in the arithmetic type, derived on the host in FP64.
+template <class R> struct Coef {
+    R nu_p, sigma_y, m, gdot_c, inv_gc, e_c, magic;
+    R g[3];
+    R s2y;     // sqrt(2) sigma_y
+    R ir_a;    // 1 / (1/2 + 3 nu_p)
+    R ir_b;    // 1 / (1 + 6 nu_p)
+    R six_nu;  // 6 nu_p
+};
+
+struct KArgs {
+    KParams kp;
+    Coef<float> cf;
+    Coef<double> cd;
+};
+
+template <class R> __device__ __forceinline__ const Coef<R>& coef(const KArgs& a);
+template <> __device__ __forceinline__ const Coef<float>& coef<float>(const KArgs& a) { return a.cf; }
+template <> __device__ __forceinline__ const Coef<double>& coef<double>(const KArgs& a) { return a.cd; }
+
+// ---------------------------------------------------------------------------
+// streaming (pull) with halfway bounce-back
+template <class L, class S>
+__device__ __forceinline__ void gather(const KParams& kp, const S* __restrict__ f, uint32_t lk,
+                                       int idx, typename Store<S>::R (&v)[L::Q]) {
+    const int nx = kp.nx, ny = kp.ny, nz = kp.nz;
+    const int x = idx % nx;
+    const int t = idx / nx;
+    const int y = t % ny;
+    const int z = t / ny;
+    // offsets from idx to the source cell x - c for c = +1 (m) and c = -1 (p)
+    const int sy = nx, sz = nx * ny;
+    const int dxm = (x == 0) ? nx - 1 : -1;
+    const int dxp = (x == nx - 1) ? -(nx - 1) : 1;
+    const int dym = (y == 0) ? (ny - 1) * sy : -sy;
+    const int dyp = (y == ny - 1) ? -(ny - 1) * sy : sy;
+    const int dzm = (z == 0) ? (nz - 1) * sz : -sz;
+    const int dzp = (z == nz - 1) ? -(nz - 1) * sz : sz;
+    const int64_t plane = kp.plane;
+    static_for<0, L::Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        constexpr int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
+        int off = 0;
+        if constexpr (cx > 0) off += dxm;
+        if constexpr (cx < 0) off += dxp;
+        if constexpr (cy > 0) off += dym;
+        if constexpr (cy < 0) off += dyp;
+        if constexpr (cz > 0) off += dzm;
+        if constexpr (cz < 0) off += dzp;
+        const S* p = ((lk >> i) & 1u) ? (f + (int64_t)L::opp(i) * plane + idx)
+                                      : (f + (int64_t)i * plane + (idx + off));
+        v[i] = Store<S>::ld(p);
+    });
+}
+
+// ---------------------------------------------------------------------------
+// moments of the offsets: d = sum df, j = sum c df, p = sum c c df
+template <class R> struct Mom {
+    R d, jx, jy, jz, xx, yy, zz, xy, xz, yz;
+};
+
+template <class L, class R>
+__device__ __forceinline__ Mom<R> moments(const R (&f)[L::Q]) {
+    Mom<R> m{R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
+    static_for<0, L::Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        constexpr int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
+        const R v = f[i];
+        m.d += v;
+        if constexpr (cx == 1) m.jx += v;
+        if constexpr (cx == -1) m.jx -= v;
+        if constexpr (cy == 1) m.jy += v;
+        if constexpr (cy == -1) m.jy -= v;
+        if constexpr (cz == 1) m.jz += v;
+        if constexpr (cz == -1) m.jz -= v;
+        if constexpr (cx != 0) m.xx += v;
+        if constexpr (cy != 0) m.yy += v;
+        if constexpr (cz != 0) m.zz += v;
+        if constexpr (cx * cy == 1) m.xy += v;
+        if constexpr (cx * cy == -1) m.xy -= v;
+        if constexpr (cx * cz == 1) m.xz += v;
+        if constexpr (cx * cz == -1) m.xz -= v;
+        if constexpr (cy * cz == 1) m.yz += v;
+        if constexpr (cy * cz == -1) m.yz -= v;
+    });
+    return m;
+}
+
+// Non-equilibrium second moment T = Pi - rho c_s^2 I - rho u u written with
+// offsets: Pi = c_s^2 I + p, rho = 1 + d.
+template <class L, class R> struct Tens {
+    R xx, yy, zz, xy, xz, yz;
+};
+
+template <class L, class R>
+__device__ __forceinline__ Tens<L, R> noneq(const Mom<R>& m, R rho, R ux, R uy, R uz, uint32_t flags) {
+    const R third = R(1.0 / 3.0);
+    Tens<L, R> t;
+    t.xx = m.xx - m.d * third - rho * ux * ux;
+    t.yy = m.yy - m.d * third - rho * uy * uy;
+    t.xy = m.xy - rho * ux * uy;
+    if constexpr (L::D == 3) {
+        t.zz = m.zz - m.d * third - rho * uz * uz;
+        t.xz = m.xz - rho * ux * uz;
+        t.yz = m.yz - rho * uy * uz;
+    } else {
+        t.zz = R(0);
+        t.xz = R(0);
+        t.yz = R(0);
+    }
+    if (flags & LBM_FLAG_BURNETT_X) t.xx = R(0);
+    return t;
+}
+
+// ---------------------------------------------------------------------------
+// IR collision (Secs. 2.3, 3.2).  f: offsets in, offsets out.
+template <class L, class R>
+__device__ __forceinline__ void collide_ir(const Coef<R>& c, uint32_t flags, R (&f)[L::Q],
+                                           R& drho, R (&ur)[3]) {
+    const Mom<R> m = moments<L, R>(f);
+    const R rho = R(1) + m.d;
+    const R inv = R(1) / rho;
+    const R Fx = rho * c.g[0], Fy = rho * c.g[1], Fz = (L::D == 3) ? rho * c.g[2] : R(0);
+    const R ux = (m.jx + R(0.5) * Fx) * inv;
+    const R uy = (m.jy + R(0.5) * Fy) * inv;
+    const R uz = (L::D == 3) ? (m.jz + R(0.5) * Fz) * inv : R(0);
+    const Tens<L, R> T = noneq<L, R>(m, rho, ux, uy, uz, flags);
+    const R tn2 = T.xx * T.xx + T.yy * T.yy + T.zz * T.zz +
+                  R(2) * (T.xy * T.xy + T.xz * T.xz + T.yz * T.yz);
+    const R tn = sqrt(tn2);
+    // s = as T, sigma = asg T  (eq. Vikh_sigmaS_tensor)
+    R as = R(0), asg = R(-1);
+    if (tn > R(0) && tn >= c.s2y) {
+        const R it = R(1) / tn;
+        as = -(tn - c.s2y) * c.ir_a * it;
+        asg = -(c.six_nu * tn + c.s2y) * c.ir_b * it;
+    }
+    // A = -sigma_bar + s/2 = k1 T + k2 I with sigma_bar = sigma - tr(sigma)/D I
+    const R third = R(1.0 / 3.0);
+    const R trT = T.xx + T.yy + T.zz;
+    const R k1 = R(0.5) * as - asg;
+    const R k2 = asg * trT * R(1.0 / L::D);
+    // (c c - c_s^2 I):A = k1 (cTc - trT/3) + k2 (|c|^2 - D/3) = h0 + k1 cTc + k2 |c|^2
+    const R h0 = -(k1 * trT + k2 * R(L::D)) * third;
+    const R uu = ux * ux + uy * uy + uz * uz;
+    const R base = m.d - R(1.5) * rho * uu;
+    const R r45 = R(4.5) * rho, r3 = R(3) * rho;
+    f[0] = R(L::w(0)) * (base + R(4.5) * h0);
+    static_for<0, (L::Q - 1) / 2>([&](auto P) {
+        constexpr int i = 2 * decltype(P)::value + 1;
+        constexpr int o = i + 1;
+        constexpr int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
+        constexpr int c2 = cx * cx + cy * cy + cz * cz;
+        const R w = R(L::w(i));
+        const R cu = R(cx) * ux + R(cy) * uy + R(cz) * uz;
+        const R cF = R(cx) * Fx + R(cy) * Fy + R(cz) * Fz;
+        const R cTc = R(cx * cx) * T.xx + R(cy * cy) * T.yy + R(cz * cz) * T.zz +
+                      R(2 * cx * cy) * T.xy + R(2 * cx * cz) * T.xz + R(2 * cy * cz) * T.yz;
+        const R h = h0 + k1 * cTc + k2 * R(c2);
+        const R e = w * (base + r45 * cu * cu + R(4.5) * h);
+        const R od = w * (r3 * cu + R(1.5) * cF);
+        f[i] = e + od;
+        f[o] = e - od;
+    });
+    drho = m.d;
+    ur[0] = ux;
+    ur[1] = uy;
+    ur[2] = uz;
+}
+
+// ---------------------------------------------------------------------------
+// PR collision (Sec. 3.1 + TRT + EDM).  tau: previous step's relaxation time
+// in, this step's out.
+template <class L, class R>
+__device__ __forceinline__ void collide_pr(const Coef<R>& c, uint32_t flags, R (&f)[L::Q], R& tau,
+                                           R& drho, R (&ur)[3]) {
+    const Mom<R> m = moments<L, R>(f);
+    const R rho = R(1) + m.d;
+    const R inv = R(1) / rho;
+    const R ux = m.jx * inv, uy = m.jy * inv, uz = (L::D == 3) ? m.jz * inv : R(0);
+    const Tens<L, R> T = noneq<L, R>(m, rho, ux, uy, uz, flags);
+    const R tn2 = T.xx * T.xx + T.yy * T.yy + T.zz * T.zz +
+                  R(2) * (T.xy * T.xy + T.xz * T.xz + T.yz * T.yz);
+    // D = -T / (2 tau_old c_s^2) = -1.5 T / tau_old ; gdot = sqrt(2 D:D)
+    const R gd = R(1.5) / tau * sqrt(R(2) * tn2);
+    const R sy_rho = c.sigma_y * inv;
+    R nu;
+    if (gd >= c.gdot_c) {
+        nu = c.nu_p + sy_rho * (-expm1(-c.m * gd)) / gd;
+    } else {
+        const R nu0 = c.nu_p + c.m * sy_rho;
+        const R nuc = c.nu_p + sy_rho * c.e_c;
+        nu = (c.gdot_c - gd) * c.inv_gc * nu0 + gd * c.inv_gc * nuc;
+    }
+    const R tn = R(0.5) + R(3) * nu;
+    const R wp = R(1) / tn;
+    const R wm = R(1) / (R(0.5) + c.magic / (tn - R(0.5)));
+    tau = tn;
+    const R gx = c.g[0], gy = c.g[1], gz = (L::D == 3) ? c.g[2] : R(0);
+    const R uu = ux * ux + uy * uy + uz * uz;
+    const R ug = ux * gx + uy * gy + uz * gz;
+    const R gg = gx * gx + gy * gy + gz * gz;
+    const R base = m.d - R(1.5) * rho * uu;                 // even part of f_eq - w, direction-free
+    const R fbase = R(-1.5) * rho * (R(2) * ug + gg);      // even part of the EDM difference
+    const R r45 = R(4.5) * rho, r3 = R(3) * rho;
+    {
+        const R w0 = R(L::w(0));
+        f[0] = f[0] - wp * (f[0] - w0 * base) + w0 * fbase;
+    }
+    static_for<0, (L::Q - 1) / 2>([&](auto P) {
+        constexpr int i = 2 * decltype(P)::value + 1;
+        constexpr int o = i + 1;
+        constexpr int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
+        const R w = R(L::w(i));
+        const R cu = R(cx) * ux + R(cy) * uy + R(cz) * uz;
+        const R cg = R(cx) * gx + R(cy) * gy + R(cz) * gz;
+        const R fe = R(0.5) * (f[i] + f[o]);
+        const R fo = R(0.5) * (f[i] - f[o]);
+        const R eqe = w * (base + r45 * cu * cu);
+        const R eqo = w * (r3 * cu);
+        const R Fe = w * (fbase + r45 * cg * (R(2) * cu + cg));
+        const R Fo = w * (r3 * cg);
+        const R E = fe - wp * (fe - eqe) + Fe;
+        const R O = fo - wm * (fo - eqo) + Fo;
+        f[i] = E + O;
+        f[o] = E - O;
+    });
+    drho = m.d;
+    ur[0] = ux + R(0.5) * gx;
+    ur[1] = uy + R(0.5) * gy;
+    ur[2] = uz + R(0.5) * gz;
+}
+
+// ---------------------------------------------------------------------------
+// deterministic block reduction of kNumStats doubles (fixed shuffle tree)
+__device__ __forceinline__ void block_sum_store(double (&v)[kNumStats], double* __restrict__ out) {
+    __shared__ double sm[kBlock / 32][kNumStats];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < kNumStats; ++k) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < kNumStats; ++k) sm[warp][k] = v[k];
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < kNumStats; ++k) {
+            double t = (lane < kBlock / 32) ? sm[lane][k] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+            if (lane == 0) out[k] = t;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// the fused step
+template <class L, int MODEL, class S, bool CHECK>
+__global__ void __launch_bounds__(kBlock)
+k_step(const KArgs a, const S* __restrict__ fsrc, S* __restrict__ fdst,
+       const uint32_t* __restrict__ links, typename Store<S>::R* __restrict__ tau,
+       typename Store<S>::R* __restrict__ usnap, double* __restrict__ partials) {
+    using R = typename Store<S>::R;
+    const KParams& kp = a.kp;
+    const int idx = blockIdx.x * kBlock + threadIdx.x;
+    const bool inside = idx < kp.ncells;
+    const uint32_t lk = inside ? __ldg(links + idx) : kSolidBit;
+    const bool active = !(lk & kSolidBit);
+    if constexpr (!CHECK) {
+        if (!active) return;
+    }
+    double acc[kNumStats];
+    if constexpr (CHECK) {
+#pragma unroll
+        for (int k = 0; k < kNumStats; ++k) acc[k] = 0.0;
+    }
+    if (active) {
+        R f[L::Q];
+        gather<L, S>(kp, fsrc, lk, idx, f);
+        R drho, ur[3];
+        if constexpr (MODEL == LBM_MODEL_PR) {
+            R t = tau[idx];
+            collide_pr<L, R>(coef<R>(a), kp.flags, f, t, drho, ur);
+            tau[idx] = t;
+        } else {
+            collide_ir<L, R>(coef<R>(a), kp.flags, f, drho, ur);
+        }
+        const int64_t plane = kp.plane;
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) Store<S>::st(fdst + (int64_t)i * plane + idx, f[i]);
+        if constexpr (CHECK) {
+            double du2 = 0.0, u2 = 0.0;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const double u = (double)ur[d];
+                const double up = (double)usnap[(int64_t)d * plane + idx];
+                acc[kStatUx + d] = u;
+                du2 += (u - up) * (u - up);
+                u2 += u * u;
+                usnap[(int64_t)d * plane + idx] = ur[d];
+            }
+            acc[kStatDu2] = du2;
+            acc[kStatU2] = u2;
+            acc[kStatDrho] = (double)drho;
+            acc[kStatNonFinite] = isfinite((double)drho) ? 0.0 : 1.0;
+        }
+    }
+    if constexpr (CHECK) block_sum_store(acc, partials + (int64_t)blockIdx.x * kNumStats);
+}
+
+// macroscopic fields of the streamed populations
+template <class L, class S>
+__global__ void __launch_bounds__(kBlock)
+k_fields(const KArgs a, const S* __restrict__ f, const uint32_t* __restrict__ links,
+         double* __restrict__ rho, double* __restrict__ ux, double* __restrict__ uy,
+         double* __restrict__ uz) {
+    using R = typename Store<S>::R;
+    const KParams& kp = a.kp;
+    const int idx = blockIdx.x * kBlock + threadIdx.x;
+    if (idx >= kp.ncells) return;
+    const uint32_t lk = links[idx];
+    double r = 0.0, u[3] = {0.0, 0.0, 0.0};
+    if (!(lk & kSolidBit)) {
+        R v[L::Q];
+        gather<L, S>(kp, f, lk, idx, v);
+        const Mom<R> m = moments<L, R>(v);
+        const Coef<R>& c = coef<R>(a);
+        const R rr = R(1) + m.d;
+        const R inv = R(1) / rr;
+        r = (double)rr;
+        u[0] = (double)((m.jx + R(0.5) * rr * c.g[0]) * inv);
+        u[1] = (double)((m.jy + R(0.5) * rr * c.g[1]) * inv);
+        if constexpr (L::D == 3) u[2] = (double)((m.jz + R(0.5) * rr * c.g[2]) * inv);
+    }
+    if (rho) rho[idx] = r;
+    if (ux) ux[idx] = u[0];
+    if (uy) uy[idx] = u[1];
+    if (uz) uz[idx] = u[2];
+}
+
+// grid-stride reductions: flow sums of u_real (gathered) or state totals
+template <class L, class S, int MODE>
+__global__ void __launch_bounds__(kBlock)
+k_reduce(const KArgs a, const S* __restrict__ f, const uint32_t* __restrict__ links,
+         double* __restrict__ partials) {
+    using R = typename Store<S>::R;
+    const KParams& kp = a.kp;
+    double acc[kNumStats];
+#pragma unroll
+    for (int k = 0; k < kNumStats; ++k) acc[k] = 0.0;
+    const int stride = gridDim.x * kBlock;
+    for (int idx = blockIdx.x * kBlock + threadIdx.x; idx < kp.ncells; idx += stride) {
+        const uint32_t lk = links[idx];
+        if (lk & kSolidBit) continue;
+        R v[L::Q];
+        if constexpr (MODE == kReduceFlow) {
+            gather<L, S>(kp, f, lk, idx, v);
+        } else {
+#pragma unroll
+            for (int i = 0; i < L::Q; ++i) v[i] = Store<S>::ld(f + (int64_t)i * kp.plane + idx);
+        }
+        const Mom<R> m = moments<L, R>(v);
+        if constexpr (MODE == kReduceFlow) {
+            const Coef<R>& c = coef<R>(a);
+            const R rr = R(1) + m.d;
+            const R inv = R(1) / rr;
+            acc[kStatUx] += (double)((m.jx + R(0.5) * rr * c.g[0]) * inv);
+            acc[kStatUy] += (double)((m.jy + R(0.5) * rr * c.g[1]) * inv);
+            if constexpr (L::D == 3) acc[kStatUz] += (double)((m.jz + R(0.5) * rr * c.g[2]) * inv);
+            acc[kStatDrho] += (double)m.d;
+        } else {
+            acc[kTotMass] += (double)m.d;
+            acc[kTotJx] += (double)m.jx;
+            acc[kTotJy] += (double)m.jy;
+            acc[kTotJz] += (double)m.jz;
+        }
+    }
+    block_sum_store(acc, partials + (int64_t)blockIdx.x * kNumStats);
+}
+
+// solid / bounce-back link bits: bit i set if the cell at x - c_i is solid
+template <class L>
+__global__ void __launch_bounds__(kBlock)
+k_links(const KParams kp, const uint8_t* __restrict__ mask, uint32_t* __restrict__ links) {
+    const int idx = blockIdx.x * kBlock + threadIdx.x;
+    if (idx >= kp.ncells) return;
+    if (mask[idx]) {
+        links[idx] = kSolidBit;
+        return;
+    }
+    const int nx = kp.nx, ny = kp.ny, nz = kp.nz;
+    const int x = idx % nx, t = idx / nx, y = t % ny, z = t / ny;
+    uint32_t bits = 0;
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+        const int xs = (x - L::cx(i) + nx) % nx;
+        const int ys = (y - L::cy(i) + ny) % ny;
+        const int zs = (z - L::cz(i) + nz) % nz;
+        if (mask[xs + nx * (ys + ny * zs)]) bits |= 1u << i;
+    }
+    links[idx] = bits;
+}
+
+// FP64 full populations <-> stored offsets, one population plane at a time
+template <class L, class S>
+__global__ void __launch_bounds__(kBlock)
+k_convert(const KParams kp, int q, bool to_device, S* __restrict__ f, double* __restrict__ buf) {
+    const int idx = blockIdx.x * kBlock + threadIdx.x;
+    if (idx >= kp.ncells) return;
+    double w = 0.0;
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i)
+        if (i == q) w = L::w(i);
+    S* p = f + (int64_t)q * kp.plane + idx;
+    if (to_device)
+        *p = (S)(buf[idx] - w);
+    else
+        buf[idx] = (double)*p + w;
+}
+
+// ---------------------------------------------------------------------------
+// host-side helpers for the per-lattice launchers
+template <class R> inline Coef<R> make_coef(const KParams& kp) {
+    Coef<R> c;
+    const double nu = kp.nu_p;
+    c.nu_p = (R)nu;
+    c.sigma_y = (R)kp.sigma_y;
+    c.m = (R)kp.m;
+    c.gdot_c = (R)kp.gdot_c;
+    c.inv_gc = (R)(1.0 / kp.gdot_c);
+    c.e_c = (R)(kp.m * kp.gdot_c > 0.0 ? -expm1(-kp.m * kp.gdot_c) / kp.gdot_c : 0.0);
+    c.magic = (R)kp.magic;
+    for (int d = 0; d < 3; ++d) c.g[d] = (R)kp.g[d];
+    c.s2y = (R)(1.4142135623730951 * kp.sigma_y);
+    c.ir_a = (R)(1.0 / (0.5 + 3.0 * nu));
+    c.ir_b = (R)(1.0 / (1.0 + 6.0 * nu));
+    c.six_nu = (R)(6.0 * nu);
+    return c;
+}
+
+inline KArgs make_args(const KParams& kp) {
+    KArgs a;
+    a.kp = kp;
+    a.cf = make_coef<float>(kp);
+    a.cd = make_coef<double>(kp);
+    return a;
+}
+
+template <class L, int MODEL, class S>
+cudaError_t launch_step_t(bool check, const KParams& kp, const StepArgs& s, cudaStream_t st) {
+    using R = typename Store<S>::R;
+    const KArgs a = make_args(kp);
+    const int grid = step_grid(kp.ncells);
+    if (check)
+        k_step<L, MODEL, S, true><<<grid, kBlock, 0, st>>>(
+            a, (const S*)s.fsrc, (S*)s.fdst, s.links, (R*)s.tau, (R*)s.usnap, s.partials);
+    else
+        k_step<L, MODEL, S, false><<<grid, kBlock, 0, st>>>(
+            a, (const S*)s.fsrc, (S*)s.fdst, s.links, (R*)s.tau, (R*)s.usnap, s.partials);
+    return cudaGetLastError();
+}
+
+template <class L, class S>
+cudaError_t launch_step_model(int model, bool check, const KParams& kp, const StepArgs& s,
+                              cudaStream_t st) {
+    if (model == LBM_MODEL_PR) return launch_step_t<L, LBM_MODEL_PR, S>(check, kp, s, st);
+    return launch_step_t<L, LBM_MODEL_IR, S>(check, kp, s, st);
+}
+
+template <class L>
+cudaError_t launch_step_lat(int model, int storage, bool check, const KParams& kp,
+                            const StepArgs& s, cudaStream_t st) {
+    switch (storage) {
+    case LBM_F32: return launch_step_model<L, float>(model, check, kp, s, st);
+    case LBM_F64: return launch_step_model<L, double>(model, check, kp, s, st);
+    default: return cudaErrorNotSupported;
+    }
+}
+
+template <class L>
+cudaError_t launch_links_lat(const KParams& kp, const uint8_t* mask, uint32_t* links,
+                             cudaStream_t st) {
+    k_links<L><<<step_grid(kp.ncells), kBlock, 0, st>>>(kp, mask, links);
+    return cudaGetLastError();
+}
+
+template <class L>
+cudaError_t launch_fields_lat(int storage, const KParams& kp, const void* f, const uint32_t* links,
+                              double* rho, double* ux, double* uy, double* uz, cudaStream_t st) {
+    const KArgs a = make_args(kp);
+    const int grid = step_grid(kp.ncells);
+    switch (storage) {
+    case LBM_F32:
+        k_fields<L, float><<<grid, kBlock, 0, st>>>(a, (const float*)f, links, rho, ux, uy, uz);
+        break;
+    case LBM_F64:
+        k_fields<L, double><<<grid, kBlock, 0, st>>>(a, (const double*)f, links, rho, ux, uy, uz);
+        break;
+    default: return cudaErrorNotSupported;
+    }
+    return cudaGetLastError();
+}
+
+template <class L, class S>
+cudaError_t launch_reduce_s(int mode, const KArgs& a, const void* f, const uint32_t* links,
+                            double* partials, int nblocks, cudaStream_t st) {
+    if (mode == kReduceFlow)
+        k_reduce<L, S, kReduceFlow><<<nblocks, kBlock, 0, st>>>(a, (const S*)f, links, partials);
+    else
+        k_reduce<L, S, kReduceTotals><<<nblocks, kBlock, 0, st>>>(a, (const S*)f, links, partials);
+    return cudaGetLastError();
+}
+
+template <class L>
+cudaError_t launch_reduce_lat(int storage, int mode, const KParams& kp, const void* f,
+                              const uint32_t* links, double* partials, int nblocks,
+                              cudaStream_t st) {
+    const KArgs a = make_args(kp);
+    switch (storage) {
+    case LBM_F32: return launch_reduce_s<L, float>(mode, a, f, links, partials, nblocks, st);
+    case LBM_F64: return launch_reduce_s<L, double>(mode, a, f, links, partials, nblocks, st);
+    default: return cudaErrorNotSupported;
+    }
+}
+
+template <class L>
+cudaError_t launch_convert_lat(int storage, bool to_device, const KParams& kp, int q, void* f,
+                               double* buf, cudaStream_t st) {
+    const int grid = step_grid(kp.ncells);
+    switch (storage) {
+    case LBM_F32: k_convert<L, float><<<grid, kBlock, 0, st>>>(kp, q, to_device, (float*)f, buf); break;
+    case LBM_F64: k_convert<L, double><<<grid, kBlock, 0, st>>>(kp, q, to_device, (double*)f, buf); break;
+    default: return cudaErrorNotSupported;
+    }
+    return cudaGetLastError();
+}
+
+template <class L> void lattice_table(int* c, double* w) {
+    for (int i = 0; i < L::Q; ++i) {
+        if (c) {
+            c[3 * i] = L::cx(i);
+            c[3 * i + 1] = L::cy(i);
+            c[3 * i + 2] = L::cz(i);
+        }
+        if (w) w[i] = L::w(i);
+    }
+}
+
+}  // namespace blbm
+
+#define BLBM_DEFINE_LAUNCHERS(L)                                                               \
+    namespace blbm {                                                                            \
+    cudaError_t launch_step_##L(int model, int storage, bool check, const KParams& kp,         \
+                                const StepArgs& a, cudaStream_t st) {                           \
+        return launch_step_lat<L>(model, storage, check, kp, a, st);                            \
+    }                                                                                           \
+    cudaError_t launch_links_##L(const KParams& kp, const uint8_t* mask, uint32_t* links,      \
+                                 cudaStream_t st) {                                             \
+        return launch_links_lat<L>(kp, mask, links, st);                                        \
+    }                                                                                           \
+    cudaError_t launch_fields_##L(int storage, const KParams& kp, const void* f,               \
+                                  const uint32_t* links, double* rho, double* ux, double* uy,  \
+                                  double* uz, cudaStream_t st) {                                \
+        return launch_fields_lat<L>(storage, kp, f, links, rho, ux, uy, uz, st);                \
+    }                                                                                           \
+    cudaError_t launch_reduce_##L(int storage, int mode, const KParams& kp, const void* f,     \
+                                  const uint32_t* links, double* partials, int nblocks,        \
+                                  cudaStream_t st) {                                            \
+        return launch_reduce_lat<L>(storage, mode, kp, f, links, partials, nblocks, st);        \
+    }                                                                                           \
+    cudaError_t launch_convert_##L(int storage, bool to_device, const KParams& kp, int q,      \
+                                   void* f, double* plane_buf, cudaStream_t st) {               \
+        return launch_convert_lat<L>(storage, to_device, kp, q, f, plane_buf, st);              \
+    }                                                                                           \
+    void lattice_table_##L(int* c, double* w) { lattice_table<L>(c, w); }                       \
+    }

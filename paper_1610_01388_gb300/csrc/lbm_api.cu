@@ -1,0 +1,707 @@
+// Host implementation of the C ABI declared in include/bingham_lbm.h.
+//
+// Device memory of one solver (one allocation or one caller workspace, each
+// region 256-byte aligned):
+//   f[2]      population offsets f_i - w_i, SoA [Q][plane], A/B buffers
+//   links     per-cell bounce-back bits (bit i: cell at x - c_i is solid;
+//             bit 31: the cell itself is solid)
+//   tau       PR relaxation time per cell, updated in place
+//   usnap     check-step velocity snapshot [3][plane]
+//   partials  per-block FP64 reduction partials
+//   stats     finalised reduction results
+//   mask      the uploaded solid mask (bytes)
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/bingham_lbm.h"
+#include "lbm_internal.h"
+
+using namespace blbm;
+
+namespace {
+
+thread_local std::string g_err;
+
+lbm_status fail(lbm_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+int lattice_q(int lat) {
+    switch (lat) {
+    case LBM_D2Q9: return 9;
+    case LBM_D3Q15: return 15;
+    case LBM_D3Q19: return 19;
+    case LBM_D3Q27: return 27;
+    default: return 0;
+    }
+}
+
+size_t storage_bytes(int storage) {
+    switch (storage) {
+    case LBM_F64: return 8;
+    case LBM_F32: return 4;
+    case LBM_F16_OFS:
+    case LBM_BF16_OFS: return 2;
+    default: return 0;
+    }
+}
+
+size_t arith_bytes(int storage) { return storage == LBM_F64 ? 8 : 4; }
+
+bool storage_built(int storage) { return storage == LBM_F32 || storage == LBM_F64; }
+
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+struct Layout {
+    int64_t plane;
+    size_t off_f[2], off_links, off_tau, off_usnap, off_partials, off_stats, off_mask, total;
+    int nparts;
+};
+
+Layout make_layout(int lat, int nx, int ny, int nz, const lbm_params& p) {
+    Layout L{};
+    const int64_t ncells = (int64_t)nx * ny * nz;
+    L.plane = (ncells + 63) / 64 * 64;
+    const int Q = lattice_q(lat);
+    const size_t fb = align256((size_t)Q * L.plane * storage_bytes(p.storage));
+    const size_t rs = arith_bytes(p.storage);
+    size_t o = 0;
+    L.off_f[0] = o; o += fb;
+    L.off_f[1] = o; o += fb;
+    L.off_links = o; o += align256((size_t)L.plane * 4);
+    L.off_tau = o; o += (p.model == LBM_MODEL_PR) ? align256((size_t)L.plane * rs) : 0;
+    L.off_usnap = o; o += (p.check_every > 0) ? align256((size_t)3 * L.plane * rs) : 0;
+    const int g1 = step_grid((int)ncells), g2 = reduce_grid((int)ncells);
+    L.nparts = g1 > g2 ? g1 : g2;
+    L.off_partials = o; o += align256((size_t)L.nparts * kNumStats * sizeof(double));
+    L.off_stats = o; o += align256(2 * kNumStats * sizeof(double));
+    L.off_mask = o; o += align256((size_t)ncells);
+    L.total = o;
+    return L;
+}
+
+lbm_status validate(int lat, int nx, int ny, int nz, const uint8_t* mask, const lbm_params* p) {
+    if (!p) return fail(LBM_EINVAL, "params is NULL");
+    if (lattice_q(lat) == 0) return fail(LBM_EINVAL, "unknown lattice %d", lat);
+    if (nx < 1 || ny < 1 || nz < 1) return fail(LBM_EINVAL, "extents must be >= 1 (got %d,%d,%d)", nx, ny, nz);
+    if (lat == LBM_D2Q9 && nz != 1) return fail(LBM_EINVAL, "D2Q9 needs nz == 1 (got %d)", nz);
+    const int64_t n = (int64_t)nx * ny * nz;
+    if (n > (int64_t)0x7fffffff - 64) return fail(LBM_EINVAL, "too many cells (%lld)", (long long)n);
+    if (p->model != LBM_MODEL_PR && p->model != LBM_MODEL_IR) return fail(LBM_EINVAL, "unknown model %d", p->model);
+    if (storage_bytes(p->storage) == 0) return fail(LBM_EINVAL, "unknown storage %d", p->storage);
+    if (!storage_built(p->storage)) return fail(LBM_EUNSUPPORTED, "storage %d is not built into this library", p->storage);
+    if (!(p->mu_p > 0.0) || !std::isfinite(p->mu_p)) return fail(LBM_EINVAL, "mu_p must be > 0");
+    if (!(p->sigma_y >= 0.0) || !std::isfinite(p->sigma_y)) return fail(LBM_EINVAL, "sigma_y must be >= 0");
+    if (p->model == LBM_MODEL_PR) {
+        if (!(p->m >= 0.0) || !std::isfinite(p->m)) return fail(LBM_EINVAL, "m must be >= 0");
+        if (!(p->gammadot_c > 0.0) || !std::isfinite(p->gammadot_c)) return fail(LBM_EINVAL, "gammadot_c must be > 0");
+        if (!(p->magic > 0.0) || !std::isfinite(p->magic)) return fail(LBM_EINVAL, "magic must be > 0");
+    }
+    for (int d = 0; d < 3; ++d)
+        if (!std::isfinite(p->g[d])) return fail(LBM_EINVAL, "g must be finite");
+    if (lat == LBM_D2Q9 && p->g[2] != 0.0) return fail(LBM_EINVAL, "D2Q9 needs g[2] == 0");
+    if (p->check_every < 0) return fail(LBM_EINVAL, "check_every must be >= 0");
+    if (p->flags & ~LBM_FLAG_BURNETT_X) return fail(LBM_EINVAL, "unknown flags 0x%x", p->flags);
+    if (!mask) return fail(LBM_EINVAL, "solid_mask is NULL");
+    int64_t fluid = 0;
+    for (int64_t i = 0; i < n; ++i) fluid += mask[i] == 0;
+    if (fluid == 0) return fail(LBM_EINVAL, "the mask has no fluid cell");
+    return LBM_OK;
+}
+
+}  // namespace
+
+struct lbm_solver {
+    int lat = 0, Q = 0, D = 0, nx = 0, ny = 0, nz = 0;
+    int ncells = 0;
+    int64_t nfluid = 0;
+    lbm_params p{};
+    KParams kp{};
+    Layout lay{};
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    int device = 0;
+    bool owns = false;
+    char* base = nullptr;
+    void* f[2] = {nullptr, nullptr};
+    uint32_t* links = nullptr;
+    void* tau = nullptr;
+    void* usnap = nullptr;
+    double* partials = nullptr;
+    double* stats = nullptr;
+    double* host_stats = nullptr;   // pinned, kNumStats doubles of the last check step
+    double* scratch = nullptr;      // lazily allocated: 4 x ncells doubles
+    int cur = 0;
+    int64_t steps = 0;
+    int64_t checks = 0;
+    int64_t last_check = -1;
+    bool poisoned = false;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    int graph_len = 64;
+};
+
+namespace {
+
+lbm_status cuda_fail(lbm_solver* s, cudaError_t e, const char* what) {
+    if (s) s->poisoned = true;
+    cudaGetLastError();
+    return fail(LBM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(s, expr, what)                                  \
+    do {                                                   \
+        cudaError_t e_ = (expr);                           \
+        if (e_ != cudaSuccess) return cuda_fail(s, e_, what); \
+    } while (0)
+
+lbm_status enter(const lbm_solver* s) {
+    if (!s) return fail(LBM_EINVAL, "solver is NULL");
+    if (s->poisoned) return fail(LBM_ECUDA, "solver is in an error state after a CUDA failure");
+    int dev = -1;
+    if (cudaGetDevice(&dev) == cudaSuccess && dev != s->device) cudaSetDevice(s->device);
+    return LBM_OK;
+}
+
+cudaError_t launch_step(lbm_solver* s, bool check, cudaStream_t st) {
+    StepArgs a;
+    a.fsrc = s->f[s->cur];
+    a.fdst = s->f[s->cur ^ 1];
+    a.links = s->links;
+    a.tau = s->tau;
+    a.usnap = s->usnap;
+    a.partials = s->partials;
+    switch (s->lat) {
+    case LBM_D2Q9: return launch_step_D2Q9(s->p.model, s->p.storage, check, s->kp, a, st);
+    case LBM_D3Q15: return launch_step_D3Q15(s->p.model, s->p.storage, check, s->kp, a, st);
+    case LBM_D3Q19: return launch_step_D3Q19(s->p.model, s->p.storage, check, s->kp, a, st);
+    default: return launch_step_D3Q27(s->p.model, s->p.storage, check, s->kp, a, st);
+    }
+}
+
+cudaError_t launch_links(lbm_solver* s, const uint8_t* mask) {
+    switch (s->lat) {
+    case LBM_D2Q9: return launch_links_D2Q9(s->kp, mask, s->links, s->stream);
+    case LBM_D3Q15: return launch_links_D3Q15(s->kp, mask, s->links, s->stream);
+    case LBM_D3Q19: return launch_links_D3Q19(s->kp, mask, s->links, s->stream);
+    default: return launch_links_D3Q27(s->kp, mask, s->links, s->stream);
+    }
+}
+
+cudaError_t launch_fields(lbm_solver* s, double* rho, double* ux, double* uy, double* uz) {
+    const void* f = s->f[s->cur];
+    switch (s->lat) {
+    case LBM_D2Q9: return launch_fields_D2Q9(s->p.storage, s->kp, f, s->links, rho, ux, uy, uz, s->stream);
+    case LBM_D3Q15: return launch_fields_D3Q15(s->p.storage, s->kp, f, s->links, rho, ux, uy, uz, s->stream);
+    case LBM_D3Q19: return launch_fields_D3Q19(s->p.storage, s->kp, f, s->links, rho, ux, uy, uz, s->stream);
+    default: return launch_fields_D3Q27(s->p.storage, s->kp, f, s->links, rho, ux, uy, uz, s->stream);
+    }
+}
+
+cudaError_t launch_reduce(lbm_solver* s, int mode, int nblocks) {
+    const void* f = s->f[s->cur];
+    switch (s->lat) {
+    case LBM_D2Q9: return launch_reduce_D2Q9(s->p.storage, mode, s->kp, f, s->links, s->partials, nblocks, s->stream);
+    case LBM_D3Q15: return launch_reduce_D3Q15(s->p.storage, mode, s->kp, f, s->links, s->partials, nblocks, s->stream);
+    case LBM_D3Q19: return launch_reduce_D3Q19(s->p.storage, mode, s->kp, f, s->links, s->partials, nblocks, s->stream);
+    default: return launch_reduce_D3Q27(s->p.storage, mode, s->kp, f, s->links, s->partials, nblocks, s->stream);
+    }
+}
+
+cudaError_t launch_convert(lbm_solver* s, bool to_device, int q, double* buf) {
+    void* f = s->f[s->cur];
+    switch (s->lat) {
+    case LBM_D2Q9: return launch_convert_D2Q9(s->p.storage, to_device, s->kp, q, f, buf, s->stream);
+    case LBM_D3Q15: return launch_convert_D3Q15(s->p.storage, to_device, s->kp, q, f, buf, s->stream);
+    case LBM_D3Q19: return launch_convert_D3Q19(s->p.storage, to_device, s->kp, q, f, buf, s->stream);
+    default: return launch_convert_D3Q27(s->p.storage, to_device, s->kp, q, f, buf, s->stream);
+    }
+}
+
+lbm_status ensure_scratch(lbm_solver* s) {
+    if (s->scratch) return LBM_OK;
+    void* p = nullptr;
+    if (cudaMalloc(&p, (size_t)4 * s->ncells * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LBM_ENOMEM, "cannot allocate %zu bytes of field scratch",
+                    (size_t)4 * s->ncells * sizeof(double));
+    }
+    s->scratch = (double*)p;
+    return LBM_OK;
+}
+
+// one ordinary step or check step on stream st
+cudaError_t do_step(lbm_solver* s, bool check, cudaStream_t st) {
+    cudaError_t e = launch_step(s, check, st);
+    if (e != cudaSuccess) return e;
+    s->cur ^= 1;
+    s->steps += 1;
+    if (check) {
+        e = launch_finalize(s->partials, step_grid(s->ncells), s->stats, st);
+        if (e != cudaSuccess) return e;
+        e = cudaMemcpyAsync(s->host_stats, s->stats, kNumStats * sizeof(double),
+                            cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) return e;
+        s->checks += 1;
+        s->last_check = s->steps;
+    }
+    return cudaSuccess;
+}
+
+// graph of graph_len plain steps starting from buffer parity `par`
+cudaError_t build_graph(lbm_solver* s, int par) {
+    if (!s->cap_stream) {
+        cudaError_t e = cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return e;
+    }
+    const int saved_cur = s->cur;
+    const int64_t saved_steps = s->steps;
+    s->cur = par;
+    cudaError_t e = cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    for (int k = 0; k < s->graph_len && e == cudaSuccess; ++k) e = do_step(s, false, s->cap_stream);
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(s->cap_stream, &g);
+    s->cur = saved_cur;
+    s->steps = saved_steps;
+    if (e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return e;
+    }
+    if (e2 != cudaSuccess) return e2;
+    e = cudaGraphInstantiate(&s->graph[par], g, 0);
+    cudaGraphDestroy(g);
+    return e;
+}
+
+}  // namespace
+
+namespace blbm {
+
+__global__ void k_finalize(const double* __restrict__ partials, int nparts, double* __restrict__ out) {
+    double v[kNumStats];
+#pragma unroll
+    for (int k = 0; k < kNumStats; ++k) v[k] = 0.0;
+    for (int b = threadIdx.x; b < nparts; b += kBlock) {
+#pragma unroll
+        for (int k = 0; k < kNumStats; ++k) v[k] += partials[(int64_t)b * kNumStats + k];
+    }
+    __shared__ double sm[kBlock / 32][kNumStats];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < kNumStats; ++k)
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    if (lane == 0)
+        for (int k = 0; k < kNumStats; ++k) sm[warp][k] = v[k];
+    __syncthreads();
+    if (warp == 0) {
+        for (int k = 0; k < kNumStats; ++k) {
+            double t = (lane < kBlock / 32) ? sm[lane][k] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+            if (lane == 0) out[k] = t;
+        }
+    }
+}
+
+cudaError_t launch_finalize(const double* partials, int nparts, double* out, cudaStream_t st) {
+    k_finalize<<<1, kBlock, 0, st>>>(partials, nparts, out);
+    return cudaGetLastError();
+}
+
+template <class T>
+__global__ void k_fill(T* __restrict__ p, int64_t n, T v) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+
+cudaError_t launch_fill(void* p, int64_t n, int rsize, double value, cudaStream_t st) {
+    const int grid = (int)((n + kBlock - 1) / kBlock < 4096 ? (n + kBlock - 1) / kBlock : 4096);
+    if (rsize == 8)
+        k_fill<double><<<grid, kBlock, 0, st>>>((double*)p, n, value);
+    else
+        k_fill<float><<<grid, kBlock, 0, st>>>((float*)p, n, (float)value);
+    return cudaGetLastError();
+}
+
+}  // namespace blbm
+
+// ===========================================================================
+extern "C" {
+
+const char* lbm_last_error(void) { return g_err.c_str(); }
+
+const char* lbm_status_string(lbm_status st) {
+    switch (st) {
+    case LBM_OK: return "ok";
+    case LBM_EINVAL: return "invalid argument";
+    case LBM_ENOMEM: return "out of memory";
+    case LBM_ECUDA: return "CUDA error";
+    case LBM_ENONFINITE: return "non-finite density";
+    case LBM_ETIMEOUT: return "timeout";
+    case LBM_EBUSY: return "busy";
+    case LBM_EUNSUPPORTED: return "unsupported";
+    default: return "unknown status";
+    }
+}
+
+lbm_status lbm_params_default(lbm_params* p) {
+    if (!p) return fail(LBM_EINVAL, "params is NULL");
+    std::memset(p, 0, sizeof(*p));
+    p->model = LBM_MODEL_IR;
+    p->storage = LBM_F32;
+    p->mu_p = 0.1;
+    p->gammadot_c = 1e-8;
+    p->magic = 0.25;
+    return LBM_OK;
+}
+
+lbm_status lbm_lattice_info(lbm_lattice lat, int* Q, int* D, int* c, double* w) {
+    switch (lat) {
+    case LBM_D2Q9: lattice_table_D2Q9(c, w); break;
+    case LBM_D3Q15: lattice_table_D3Q15(c, w); break;
+    case LBM_D3Q19: lattice_table_D3Q19(c, w); break;
+    case LBM_D3Q27: lattice_table_D3Q27(c, w); break;
+    default: return fail(LBM_EINVAL, "unknown lattice %d", (int)lat);
+    }
+    if (Q) *Q = lattice_q(lat);
+    if (D) *D = lat == LBM_D2Q9 ? 2 : 3;
+    return LBM_OK;
+}
+
+lbm_status lbm_workspace_bytes(lbm_lattice lat, int nx, int ny, int nz, const lbm_params* p,
+                               size_t* bytes) {
+    if (!p || !bytes) return fail(LBM_EINVAL, "NULL argument");
+    if (lattice_q(lat) == 0) return fail(LBM_EINVAL, "unknown lattice %d", (int)lat);
+    if (nx < 1 || ny < 1 || nz < 1) return fail(LBM_EINVAL, "extents must be >= 1");
+    if ((int64_t)nx * ny * nz > (int64_t)0x7fffffff - 64) return fail(LBM_EINVAL, "too many cells");
+    if (storage_bytes(p->storage) == 0) return fail(LBM_EINVAL, "unknown storage %d", p->storage);
+    *bytes = make_layout(lat, nx, ny, nz, *p).total;
+    return LBM_OK;
+}
+
+static lbm_status create_impl(lbm_solver** out, lbm_lattice lat, int nx, int ny, int nz,
+                              const uint8_t* mask, const lbm_params* p, void* stream,
+                              void* workspace, size_t ws_bytes) {
+    if (!out) return fail(LBM_EINVAL, "out is NULL");
+    *out = nullptr;
+    lbm_status v = validate(lat, nx, ny, nz, mask, p);
+    if (v != LBM_OK) return v;
+    lbm_solver* s = new (std::nothrow) lbm_solver();
+    if (!s) return fail(LBM_ENOMEM, "host allocation failed");
+    s->lat = lat;
+    s->Q = lattice_q(lat);
+    s->D = lat == LBM_D2Q9 ? 2 : 3;
+    s->nx = nx;
+    s->ny = ny;
+    s->nz = nz;
+    s->ncells = nx * ny * nz;
+    s->p = *p;
+    s->stream = (cudaStream_t)stream;
+    for (int i = 0; i < s->ncells; ++i) s->nfluid += mask[i] == 0;
+    s->lay = make_layout(lat, nx, ny, nz, *p);
+    KParams& kp = s->kp;
+    kp.nx = nx;
+    kp.ny = ny;
+    kp.nz = nz;
+    kp.ncells = s->ncells;
+    kp.plane = s->lay.plane;
+    kp.nu_p = p->mu_p;   // rho_0 = 1
+    kp.sigma_y = p->sigma_y;
+    kp.m = p->m;
+    kp.gdot_c = p->gammadot_c > 0.0 ? p->gammadot_c : 1e-8;
+    kp.magic = p->magic > 0.0 ? p->magic : 0.25;
+    for (int d = 0; d < 3; ++d) kp.g[d] = p->g[d];
+    kp.flags = p->flags;
+    kp.half_scale = 1.0;
+
+    cudaError_t e = cudaGetDevice(&s->device);
+    if (e != cudaSuccess) {
+        delete s;
+        cudaGetLastError();
+        return fail(LBM_ECUDA, "no CUDA device: %s", cudaGetErrorString(e));
+    }
+    if (workspace) {
+        if (ws_bytes < s->lay.total) {
+            delete s;
+            return fail(LBM_EINVAL, "workspace too small: %zu < %zu", ws_bytes, s->lay.total);
+        }
+        if (((uintptr_t)workspace & 255u) != 0) {
+            delete s;
+            return fail(LBM_EINVAL, "workspace must be 256-byte aligned");
+        }
+        s->base = (char*)workspace;
+        s->owns = false;
+    } else {
+        void* b = nullptr;
+        e = cudaMalloc(&b, s->lay.total);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            delete s;
+            return fail(LBM_ENOMEM, "cudaMalloc of %zu bytes failed", s->lay.total);
+        }
+        s->base = (char*)b;
+        s->owns = true;
+    }
+    s->f[0] = s->base + s->lay.off_f[0];
+    s->f[1] = s->base + s->lay.off_f[1];
+    s->links = (uint32_t*)(s->base + s->lay.off_links);
+    s->tau = p->model == LBM_MODEL_PR ? (void*)(s->base + s->lay.off_tau) : nullptr;
+    s->usnap = p->check_every > 0 ? (void*)(s->base + s->lay.off_usnap) : nullptr;
+    s->partials = (double*)(s->base + s->lay.off_partials);
+    s->stats = (double*)(s->base + s->lay.off_stats);
+    uint8_t* dmask = (uint8_t*)(s->base + s->lay.off_mask);
+
+    lbm_status rc = LBM_OK;
+    do {
+        e = cudaMallocHost(&s->host_stats, kNumStats * sizeof(double));
+        if (e != cudaSuccess) { rc = fail(LBM_ENOMEM, "pinned allocation failed"); cudaGetLastError(); s->host_stats = nullptr; break; }
+        std::memset(s->host_stats, 0, kNumStats * sizeof(double));
+        const size_t fb = (size_t)s->Q * s->lay.plane * storage_bytes(p->storage);
+        if ((e = cudaMemcpyAsync(dmask, mask, (size_t)s->ncells, cudaMemcpyHostToDevice, s->stream)) != cudaSuccess) break;
+        if ((e = launch_links(s, dmask)) != cudaSuccess) break;
+        if ((e = cudaMemsetAsync(s->f[0], 0, fb, s->stream)) != cudaSuccess) break;
+        if ((e = cudaMemsetAsync(s->f[1], 0, fb, s->stream)) != cudaSuccess) break;
+        if (s->tau) {
+            const double nu0 = p->mu_p + p->m * p->sigma_y;
+            if ((e = launch_fill(s->tau, s->lay.plane, (int)arith_bytes(p->storage), 0.5 + 3.0 * nu0, s->stream)) != cudaSuccess) break;
+        }
+        if (s->usnap) {
+            if ((e = cudaMemsetAsync(s->usnap, 0, (size_t)3 * s->lay.plane * arith_bytes(p->storage), s->stream)) != cudaSuccess) break;
+        }
+        if ((e = cudaMemsetAsync(s->stats, 0, 2 * kNumStats * sizeof(double), s->stream)) != cudaSuccess) break;
+        e = cudaStreamSynchronize(s->stream);
+    } while (0);
+    if (rc == LBM_OK && e != cudaSuccess) rc = cuda_fail(nullptr, e, "solver initialisation");
+    if (rc != LBM_OK) {
+        lbm_destroy(s);
+        return rc;
+    }
+    *out = s;
+    return LBM_OK;
+}
+
+lbm_status lbm_create(lbm_solver** out, lbm_lattice lat, int nx, int ny, int nz,
+                      const uint8_t* solid_mask, const lbm_params* p, void* cuda_stream) {
+    return create_impl(out, lat, nx, ny, nz, solid_mask, p, cuda_stream, nullptr, 0);
+}
+
+lbm_status lbm_create_with_workspace(lbm_solver** out, lbm_lattice lat, int nx, int ny, int nz,
+                                     const uint8_t* solid_mask, const lbm_params* p,
+                                     void* cuda_stream, void* workspace, size_t workspace_bytes) {
+    if (!workspace) return fail(LBM_EINVAL, "workspace is NULL");
+    return create_impl(out, lat, nx, ny, nz, solid_mask, p, cuda_stream, workspace, workspace_bytes);
+}
+
+lbm_status lbm_step(lbm_solver* s, int64_t nsteps) {
+    lbm_status v = enter(s);
+    if (v != LBM_OK) return v;
+    if (nsteps < 0) return fail(LBM_EINVAL, "nsteps must be >= 0");
+    const int64_t k = s->p.check_every;
+    int64_t left = nsteps;
+    while (left > 0) {
+        // plain steps before the next check step
+        int64_t plain = left;
+        if (k > 0) {
+            const int64_t to_check = k - (s->steps % k);   // the to_check-th step from now is a check step
+            plain = (to_check - 1 < left) ? to_check - 1 : left;
+        }
+        while (plain >= s->graph_len) {
+            if (!s->graph[s->cur]) CK(s, build_graph(s, s->cur), "CUDA graph capture");
+            CK(s, cudaGraphLaunch(s->graph[s->cur], s->stream), "cudaGraphLaunch");
+            s->steps += s->graph_len;   // graph_len is even: the parity is unchanged
+            plain -= s->graph_len;
+            left -= s->graph_len;
+        }
+        while (plain > 0) {
+            CK(s, do_step(s, false, s->stream), "step launch");
+            --plain;
+            --left;
+        }
+        if (left > 0 && k > 0) {
+            CK(s, do_step(s, true, s->stream), "check-step launch");
+            --left;
+        }
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_sync(lbm_solver* s) {
+    lbm_status v = enter(s);
+    if (v != LBM_OK) return v;
+    CK(s, cudaStreamSynchronize(s->stream), "cudaStreamSynchronize");
+    return LBM_OK;
+}
+
+lbm_status lbm_fields_device(lbm_solver* s, double* rho, double* ux, double* uy, double* uz) {
+    lbm_status v = enter(s);
+    if (v != LBM_OK) return v;
+    CK(s, launch_fields(s, rho, ux, uy, uz), "fields kernel");
+    return LBM_OK;
+}
+
+lbm_status lbm_fields(lbm_solver* s, double* rho, double* ux, double* uy, double* uz) {
+    lbm_status v = enter(s);
+    if (v != LBM_OK) return v;
+    if ((v = ensure_scratch(s)) != LBM_OK) return v;
+    const size_t n = (size_t)s->ncells;
+    double* d[4] = {s->scratch, s->scratch + n, s->scratch + 2 * n, s->scratch + 3 * n};
+    CK(s, launch_fields(s, d[0], d[1], d[2], d[3]), "fields kernel");
+    double* h[4] = {rho, ux, uy, uz};
+    for (int k = 0; k < 4; ++k)
+        if (h[k]) CK(s, cudaMemcpyAsync(h[k], d[k], n * sizeof(double), cudaMemcpyDeviceToHost, s->stream), "fields copy");
+    CK(s, cudaStreamSynchronize(s->stream), "fields sync");
+    return LBM_OK;
+}
+
+static lbm_status reduce_to_host(lbm_solver* s, int mode, double* out) {
+    const int nb = reduce_grid(s->ncells);
+    CK(s, launch_reduce(s, mode, nb), "reduction kernel");
+    CK(s, launch_finalize(s->partials, nb, s->stats + kNumStats, s->stream), "finalize kernel");
+    CK(s, cudaMemcpyAsync(out, s->stats + kNumStats, kNumStats * sizeof(double), cudaMemcpyDeviceToHost, s->stream), "reduction copy");
+    CK(s, cudaStreamSynchronize(s->stream), "reduction sync");
+    return LBM_OK;
+}
+
+lbm_status lbm_flowrate(lbm_solver* s, int axis, double* q) {
+    lbm_status v = enter(s);
+    if (v != LBM_OK) return v;
+    if (!q || axis < 0 || axis > 2) return fail(LBM_EINVAL, "axis must be 0, 1 or 2 and q non-NULL");
+    double r[kNumStats];
+    if ((v = reduce_to_host(s, kReduceFlow, r)) != LBM_OK) return v;
+    const int L = axis == 0 ? s->nx : (axis == 1 ? s->ny : s->nz);
+    *q = r[kStatUx + axis] / L;
+    return LBM_OK;
+}
+
+lbm_status lbm_totals(lbm_solver* s, double* mass, double momentum[3]) {
+    lbm_status v = enter(s);
+    if (v != LBM_OK) return v;
+    double r[kNumStats];
+    if ((v = reduce_to_host(s, kReduceTotals, r)) != LBM_OK) return v;
+    if (mass) *mass = (double)s->nfluid + r[kTotMass];
+    if (momentum) {
+        momentum[0] = r[kTotJx];
+        momentum[1] = r[kTotJy];
+        momentum[2] = r[kTotJz];
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_residual(lbm_solver* s, double* residual, int64_t* at_step, double* flow_x) {
+    lbm_status v = enter(s);
+    if (v != LBM_OK) return v;
+    CK(s, cudaStreamSynchronize(s->stream), "residual sync");
+    const double* r = s->host_stats;
+    if (at_step) *at_step = s->last_check;
+    if (flow_x) *flow_x = s->checks > 0 ? r[kStatUx] / s->nx : 0.0;
+    if (residual) *residual = (s->checks >= 2 && r[kStatU2] > 0.0) ? std::sqrt(r[kStatDu2] / r[kStatU2]) : -1.0;
+    if (s->checks > 0 && r[kStatNonFinite] != 0.0)
+        return fail(LBM_ENONFINITE, "check step %lld saw %g non-finite densities", (long long)s->last_check, r[kStatNonFinite]);
+    return LBM_OK;
+}
+
+lbm_status lbm_set_populations(lbm_solver* s, const double* f) {
+    lbm_status v = enter(s);
+    if (v != LBM_OK) return v;
+    if (!f) return fail(LBM_EINVAL, "f is NULL");
+    if ((v = ensure_scratch(s)) != LBM_OK) return v;
+    for (int q = 0; q < s->Q; ++q) {
+        CK(s, cudaMemcpyAsync(s->scratch, f + (size_t)q * s->ncells, (size_t)s->ncells * sizeof(double), cudaMemcpyHostToDevice, s->stream), "population upload");
+        CK(s, launch_convert(s, true, q, s->scratch), "population convert");
+    }
+    CK(s, cudaStreamSynchronize(s->stream), "population sync");
+    return LBM_OK;
+}
+
+lbm_status lbm_get_populations(lbm_solver* s, double* f) {
+    lbm_status v = enter(s);
+    if (v != LBM_OK) return v;
+    if (!f) return fail(LBM_EINVAL, "f is NULL");
+    if ((v = ensure_scratch(s)) != LBM_OK) return v;
+    for (int q = 0; q < s->Q; ++q) {
+        CK(s, launch_convert(s, false, q, s->scratch), "population convert");
+        CK(s, cudaMemcpyAsync(f + (size_t)q * s->ncells, s->scratch, (size_t)s->ncells * sizeof(double), cudaMemcpyDeviceToHost, s->stream), "population download");
+    }
+    CK(s, cudaStreamSynchronize(s->stream), "population sync");
+    return LBM_OK;
+}
+
+lbm_status lbm_set_tau(lbm_solver* s, const double* tau) {
+    lbm_status v = enter(s);
+    if (v != LBM_OK) return v;
+    if (!s->tau) return fail(LBM_EINVAL, "the IR model has no relaxation-time field");
+    if (!tau) return fail(LBM_EINVAL, "tau is NULL");
+    CK(s, cudaStreamSynchronize(s->stream), "tau sync");
+    if (arith_bytes(s->p.storage) == 8) {
+        CK(s, cudaMemcpy(s->tau, tau, (size_t)s->ncells * sizeof(double), cudaMemcpyHostToDevice), "tau upload");
+    } else {
+        std::vector<float> t(s->ncells);
+        for (int i = 0; i < s->ncells; ++i) t[i] = (float)tau[i];
+        CK(s, cudaMemcpy(s->tau, t.data(), (size_t)s->ncells * sizeof(float), cudaMemcpyHostToDevice), "tau upload");
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_get_tau(lbm_solver* s, double* tau) {
+    lbm_status v = enter(s);
+    if (v != LBM_OK) return v;
+    if (!s->tau) return fail(LBM_EINVAL, "the IR model has no relaxation-time field");
+    if (!tau) return fail(LBM_EINVAL, "tau is NULL");
+    CK(s, cudaStreamSynchronize(s->stream), "tau sync");
+    if (arith_bytes(s->p.storage) == 8) {
+        CK(s, cudaMemcpy(tau, s->tau, (size_t)s->ncells * sizeof(double), cudaMemcpyDeviceToHost), "tau download");
+    } else {
+        std::vector<float> t(s->ncells);
+        CK(s, cudaMemcpy(t.data(), s->tau, (size_t)s->ncells * sizeof(float), cudaMemcpyDeviceToHost), "tau download");
+        for (int i = 0; i < s->ncells; ++i) tau[i] = t[i];
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_get_info(const lbm_solver* s, lbm_info* info) {
+    if (!s || !info) return fail(LBM_EINVAL, "NULL argument");
+    info->lattice = s->lat;
+    info->Q = s->Q;
+    info->D = s->D;
+    info->nx = s->nx;
+    info->ny = s->ny;
+    info->nz = s->nz;
+    info->cells = s->ncells;
+    info->fluid_cells = s->nfluid;
+    info->steps_done = s->steps;
+    info->model = s->p.model;
+    info->storage = s->p.storage;
+    // read Q + write Q populations + own mask byte (+ tau read and write for PR)
+    const double b = 2.0 * s->Q * storage_bytes(s->p.storage) + 1.0 +
+                     (s->p.model == LBM_MODEL_PR ? 2.0 * arith_bytes(s->p.storage) : 0.0);
+    info->bytes_per_fluid_update = b;
+    info->device_bytes = s->lay.total;
+    return LBM_OK;
+}
+
+void lbm_destroy(lbm_solver* s) {
+    if (!s) return;
+    int dev = -1;
+    if (cudaGetDevice(&dev) == cudaSuccess && dev != s->device) cudaSetDevice(s->device);
+    if (s->stream || s->base) cudaStreamSynchronize(s->stream);
+    for (int k = 0; k < 2; ++k)
+        if (s->graph[k]) cudaGraphExecDestroy(s->graph[k]);
+    if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
+    if (s->scratch) cudaFree(s->scratch);
+    if (s->host_stats) cudaFreeHost(s->host_stats);
+    if (s->owns && s->base) cudaFree(s->base);
+    cudaGetLastError();
+    delete s;
+}
+
+}  // extern "C"

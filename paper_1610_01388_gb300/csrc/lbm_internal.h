@@ -1,0 +1,75 @@
+// Internal interface between the C ABI host code (lbm_api.cu) and the
+// per-lattice kernel translation units.  Plain C++ types only.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace blbm {
+
+constexpr int kBlock = 256;          // threads per block of the cell kernels
+constexpr int kNumStats = 8;         // doubles per reduction partial
+constexpr uint32_t kSolidBit = 1u << 31;
+
+// Scalars every cell kernel needs.  Rheology is given in double; each kernel
+// rounds it to its arithmetic type.
+struct KParams {
+    int nx, ny, nz;
+    int ncells;
+    int64_t plane;        // elements between population planes (>= ncells, padded)
+    double nu_p, sigma_y, m, gdot_c, magic;
+    double g[3];
+    uint32_t flags;
+    double half_scale;    // reduced-precision storage: offset scale (unused for F32/F64)
+};
+
+// Reduction slots.  Check step: flow sums of u_real (x,y,z), sum |u-u_prev|^2,
+// sum |u|^2, sum of density offsets, count of non-finite densities.
+enum { kStatUx = 0, kStatUy, kStatUz, kStatDu2, kStatU2, kStatDrho, kStatNonFinite };
+// Totals mode: mass offset, momentum x,y,z.
+enum { kTotMass = 0, kTotJx, kTotJy, kTotJz };
+
+struct StepArgs {
+    const void* fsrc;
+    void* fdst;
+    const uint32_t* links;
+    void* tau;           // PR relaxation-time field, updated in place (R per cell)
+    void* usnap;         // check step: u snapshot [3][plane] (R)
+    double* partials;    // check step: [gridDim][kNumStats]
+};
+
+enum ReduceMode { kReduceFlow = 0, kReduceTotals = 1 };
+
+// Per-lattice launchers (defined in kern_<lattice>.cu).
+#define BLBM_DECLARE_LAUNCHERS(L)                                                              \
+    cudaError_t launch_step_##L(int model, int storage, bool check, const KParams& kp,          \
+                                const StepArgs& a, cudaStream_t st);                            \
+    cudaError_t launch_links_##L(const KParams& kp, const uint8_t* mask, uint32_t* links,       \
+                                 cudaStream_t st);                                              \
+    cudaError_t launch_fields_##L(int storage, const KParams& kp, const void* f,                \
+                                  const uint32_t* links, double* rho, double* ux, double* uy,   \
+                                  double* uz, cudaStream_t st);                                 \
+    cudaError_t launch_reduce_##L(int storage, int mode, const KParams& kp, const void* f,      \
+                                  const uint32_t* links, double* partials, int nblocks,         \
+                                  cudaStream_t st);                                             \
+    cudaError_t launch_convert_##L(int storage, bool to_device, const KParams& kp, int q,       \
+                                   void* f, double* plane_buf, cudaStream_t st);                \
+    void lattice_table_##L(int* c, double* w);
+
+BLBM_DECLARE_LAUNCHERS(D2Q9)
+BLBM_DECLARE_LAUNCHERS(D3Q15)
+BLBM_DECLARE_LAUNCHERS(D3Q19)
+BLBM_DECLARE_LAUNCHERS(D3Q27)
+
+cudaError_t launch_finalize(const double* partials, int nparts, double* out, cudaStream_t st);
+cudaError_t launch_fill(void* p, int64_t n, int rsize, double value, cudaStream_t st);
+
+inline int step_grid(int ncells) { return (ncells + kBlock - 1) / kBlock; }
+inline int reduce_grid(int ncells) {
+    int g = (ncells + kBlock - 1) / kBlock;
+    return g < 1216 ? g : 1216;   // 152 SMs x 8 blocks
+}
+
+}  // namespace blbm

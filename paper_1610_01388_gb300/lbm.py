@@ -1,0 +1,348 @@
+"""Thin Python binding of the C ABI in include/bingham_lbm.h (ctypes).
+
+Functions carry the C names and do argument marshalling only; every step of
+the solver runs in libbingham_lbm.so's CUDA kernels.  There is no CPU
+fallback: if the library is missing or fails to load, every call raises.
+PyTorch, when used, only supplies device memory (the workspace tensor) and
+the CUDA stream handle.
+
+Array conventions: masks and fields are numpy arrays shaped (nz, ny, nx)
+(x fastest, matching the C layout); populations are (Q, nz, ny, nx) full
+FP64 values in the library's velocity order (``lbm_lattice_info``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbingham_lbm.so")
+
+LBM_D2Q9, LBM_D3Q15, LBM_D3Q19, LBM_D3Q27 = 0, 1, 2, 3
+LBM_MODEL_PR, LBM_MODEL_IR = 0, 1
+LBM_F64, LBM_F32, LBM_F16_OFS, LBM_BF16_OFS = 0, 1, 2, 3
+LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ENONFINITE, LBM_ETIMEOUT, LBM_EBUSY, \
+    LBM_EUNSUPPORTED = range(8)
+LBM_FLAG_BURNETT_X = 0x1
+
+LATTICES = {"D2Q9": LBM_D2Q9, "D3Q15": LBM_D3Q15, "D3Q19": LBM_D3Q19, "D3Q27": LBM_D3Q27}
+MODELS = {"PR": LBM_MODEL_PR, "IR": LBM_MODEL_IR}
+STORAGES = {"F64": LBM_F64, "F32": LBM_F32, "F16": LBM_F16_OFS, "BF16": LBM_BF16_OFS}
+EXPORTED = ["lbm_params_default", "lbm_lattice_info", "lbm_workspace_bytes", "lbm_create",
+            "lbm_create_with_workspace", "lbm_step", "lbm_sync", "lbm_fields", "lbm_fields_device",
+            "lbm_flowrate", "lbm_totals", "lbm_residual", "lbm_set_populations",
+            "lbm_get_populations", "lbm_set_tau", "lbm_get_tau", "lbm_get_info", "lbm_destroy",
+            "lbm_last_error", "lbm_status_string"]
+
+
+class LbmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"[{status}] {msg}")
+        self.status = status
+
+
+class lbm_params(ctypes.Structure):
+    _fields_ = [("model", ctypes.c_int32), ("storage", ctypes.c_int32),
+                ("mu_p", ctypes.c_double), ("sigma_y", ctypes.c_double),
+                ("m", ctypes.c_double), ("gammadot_c", ctypes.c_double),
+                ("g", ctypes.c_double * 3), ("magic", ctypes.c_double),
+                ("check_every", ctypes.c_int32), ("flags", ctypes.c_uint32)]
+
+
+class lbm_info(ctypes.Structure):
+    _fields_ = [("lattice", ctypes.c_int32), ("Q", ctypes.c_int32), ("D", ctypes.c_int32),
+                ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("cells", ctypes.c_int64), ("fluid_cells", ctypes.c_int64),
+                ("steps_done", ctypes.c_int64), ("model", ctypes.c_int32),
+                ("storage", ctypes.c_int32), ("bytes_per_fluid_update", ctypes.c_double),
+                ("device_bytes", ctypes.c_size_t)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library():
+    """Load libbingham_lbm.so (raises if it is not built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise LbmError(LBM_EUNSUPPORTED,
+                           f"CUDA library not built: {LIB_PATH} is missing "
+                           "(run __graft_entry__.build())")
+        lib = ctypes.CDLL(LIB_PATH)
+        P, vp = ctypes.POINTER, ctypes.c_void_p
+        i32, i64, d, sz = ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_size_t
+        sig = {
+            "lbm_params_default": [P(lbm_params)],
+            "lbm_lattice_info": [i32, P(i32), P(i32), vp, vp],
+            "lbm_workspace_bytes": [i32, i32, i32, i32, P(lbm_params), P(sz)],
+            "lbm_create": [P(vp), i32, i32, i32, i32, vp, P(lbm_params), vp],
+            "lbm_create_with_workspace": [P(vp), i32, i32, i32, i32, vp, P(lbm_params), vp, vp, sz],
+            "lbm_step": [vp, i64],
+            "lbm_sync": [vp],
+            "lbm_fields": [vp, vp, vp, vp, vp],
+            "lbm_fields_device": [vp, vp, vp, vp, vp],
+            "lbm_flowrate": [vp, i32, P(d)],
+            "lbm_totals": [vp, P(d), vp],
+            "lbm_residual": [vp, P(d), P(i64), P(d)],
+            "lbm_set_populations": [vp, vp],
+            "lbm_get_populations": [vp, vp],
+            "lbm_set_tau": [vp, vp],
+            "lbm_get_tau": [vp, vp],
+            "lbm_get_info": [vp, P(lbm_info)],
+        }
+        for name, args in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_int
+        lib.lbm_destroy.argtypes = [vp]
+        lib.lbm_destroy.restype = None
+        lib.lbm_last_error.restype = ctypes.c_char_p
+        lib.lbm_status_string.restype = ctypes.c_char_p
+        lib.lbm_status_string.argtypes = [ctypes.c_int]
+        _lib = lib
+        return lib
+
+
+def _check(st):
+    if st != LBM_OK:
+        msg = library().lbm_last_error().decode(errors="replace")
+        raise LbmError(st, msg)
+
+
+def _ptr(a):
+    return None if a is None else ctypes.c_void_p(a.ctypes.data)
+
+
+def _lat(x):
+    return LATTICES[x] if isinstance(x, str) else int(x)
+
+
+# --- C-named functions ------------------------------------------------------
+
+def lbm_params_default(**kw) -> lbm_params:
+    p = lbm_params()
+    _check(library().lbm_params_default(ctypes.byref(p)))
+    for k, v in kw.items():
+        if k == "g":
+            gg = list(v) + [0.0] * (3 - len(v))
+            p.g = (ctypes.c_double * 3)(*gg)
+        elif k == "model":
+            p.model = MODELS[v] if isinstance(v, str) else int(v)
+        elif k == "storage":
+            p.storage = STORAGES[v] if isinstance(v, str) else int(v)
+        else:
+            setattr(p, k, v)
+    return p
+
+
+def lbm_lattice_info(lat):
+    lib = library()
+    Q, D = ctypes.c_int(), ctypes.c_int()
+    _check(lib.lbm_lattice_info(_lat(lat), ctypes.byref(Q), ctypes.byref(D), None, None))
+    c = np.zeros((Q.value, 3), np.int32)
+    w = np.zeros(Q.value, np.float64)
+    _check(lib.lbm_lattice_info(_lat(lat), ctypes.byref(Q), ctypes.byref(D), _ptr(c), _ptr(w)))
+    return c, w
+
+
+def lbm_workspace_bytes(lat, nx, ny, nz, params) -> int:
+    b = ctypes.c_size_t()
+    _check(library().lbm_workspace_bytes(_lat(lat), nx, ny, nz, ctypes.byref(params),
+                                         ctypes.byref(b)))
+    return b.value
+
+
+def lbm_create(lat, mask, params, stream=None, workspace=None):
+    """mask: uint8 (nz, ny, nx) or (ny, nx); stream: int handle or None;
+    workspace: (device pointer, bytes) or None."""
+    mask = np.ascontiguousarray(mask, np.uint8)
+    if mask.ndim == 2:
+        mask = mask[None]
+    nz, ny, nx = mask.shape
+    h = ctypes.c_void_p()
+    lib = library()
+    if workspace is None:
+        _check(lib.lbm_create(ctypes.byref(h), _lat(lat), nx, ny, nz, _ptr(mask),
+                              ctypes.byref(params), ctypes.c_void_p(stream or 0)))
+    else:
+        ptr, nbytes = workspace
+        _check(lib.lbm_create_with_workspace(ctypes.byref(h), _lat(lat), nx, ny, nz, _ptr(mask),
+                                             ctypes.byref(params), ctypes.c_void_p(stream or 0),
+                                             ctypes.c_void_p(ptr), nbytes))
+    return h
+
+
+def lbm_step(h, n):
+    _check(library().lbm_step(h, int(n)))
+
+
+def lbm_sync(h):
+    _check(library().lbm_sync(h))
+
+
+def lbm_get_info(h) -> lbm_info:
+    i = lbm_info()
+    _check(library().lbm_get_info(h, ctypes.byref(i)))
+    return i
+
+
+def lbm_fields(h):
+    inf = lbm_get_info(h)
+    n = inf.cells
+    rho = np.empty(n, np.float64)
+    u = np.empty((3, n), np.float64)
+    _check(library().lbm_fields(h, _ptr(rho), _ptr(u[0]), _ptr(u[1]), _ptr(u[2])))
+    shp = (inf.nz, inf.ny, inf.nx)
+    return rho.reshape(shp), u.reshape((3,) + shp)
+
+
+def lbm_fields_device(h, rho_ptr, ux_ptr, uy_ptr, uz_ptr):
+    vp = ctypes.c_void_p
+    _check(library().lbm_fields_device(h, vp(rho_ptr), vp(ux_ptr), vp(uy_ptr), vp(uz_ptr)))
+
+
+def lbm_flowrate(h, axis=0) -> float:
+    q = ctypes.c_double()
+    _check(library().lbm_flowrate(h, int(axis), ctypes.byref(q)))
+    return q.value
+
+
+def lbm_totals(h):
+    m = ctypes.c_double()
+    j = np.zeros(3, np.float64)
+    _check(library().lbm_totals(h, ctypes.byref(m), _ptr(j)))
+    return m.value, j
+
+
+def lbm_residual(h):
+    """(residual, step index, flow rate along x) of the last check step.
+    Raises LbmError(LBM_ENONFINITE) if that check step saw a non-finite density."""
+    r, s, q = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double()
+    _check(library().lbm_residual(h, ctypes.byref(r), ctypes.byref(s), ctypes.byref(q)))
+    return r.value, s.value, q.value
+
+
+def lbm_set_populations(h, f):
+    f = np.ascontiguousarray(f, np.float64)
+    inf = lbm_get_info(h)
+    if f.size != inf.Q * inf.cells:
+        raise LbmError(LBM_EINVAL, f"populations must have {inf.Q * inf.cells} values")
+    _check(library().lbm_set_populations(h, _ptr(f)))
+
+
+def lbm_get_populations(h):
+    inf = lbm_get_info(h)
+    f = np.empty((inf.Q, inf.nz, inf.ny, inf.nx), np.float64)
+    _check(library().lbm_get_populations(h, _ptr(f)))
+    return f
+
+
+def lbm_set_tau(h, tau):
+    tau = np.ascontiguousarray(tau, np.float64)
+    _check(library().lbm_set_tau(h, _ptr(tau)))
+
+
+def lbm_get_tau(h):
+    inf = lbm_get_info(h)
+    t = np.empty((inf.nz, inf.ny, inf.nx), np.float64)
+    _check(library().lbm_get_tau(h, _ptr(t)))
+    return t
+
+
+def lbm_destroy(h):
+    if h:
+        library().lbm_destroy(h)
+
+
+# --- convenience wrapper ----------------------------------------------------
+
+class Solver:
+    """One domain on the current CUDA device.
+
+    With ``use_torch=True`` the device memory is a torch uint8 tensor (kept
+    alive by this object) and work goes to torch's current stream; otherwise
+    the library allocates with cudaMalloc and uses the legacy default stream.
+    """
+
+    def __init__(self, lattice, mask, model="IR", storage="F32", mu_p=0.1, sigma_y=0.0, m=0.0,
+                 gammadot_c=1e-8, g=(0.0, 0.0, 0.0), magic=0.25, check_every=0, flags=0,
+                 use_torch=False, stream=None):
+        self.lattice = lattice
+        self.params = lbm_params_default(model=model, storage=storage, mu_p=mu_p,
+                                         sigma_y=sigma_y, m=m, gammadot_c=gammadot_c, g=g,
+                                         magic=magic, check_every=check_every, flags=flags)
+        mask = np.ascontiguousarray(mask, np.uint8)
+        if mask.ndim == 2:
+            mask = mask[None]
+        self.mask = mask
+        self._ws = None
+        ws = None
+        if use_torch:
+            import torch
+            nz, ny, nx = mask.shape
+            nb = lbm_workspace_bytes(lattice, nx, ny, nz, self.params)
+            self._ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+            ws = (self._ws.data_ptr(), nb)
+            if stream is None:
+                stream = torch.cuda.current_stream().cuda_stream
+        self.h = lbm_create(lattice, mask, self.params, stream=stream, workspace=ws)
+        self.info = lbm_get_info(self.h)
+
+    def step(self, n=1):
+        lbm_step(self.h, n)
+
+    def sync(self):
+        lbm_sync(self.h)
+
+    def fields(self):
+        return lbm_fields(self.h)
+
+    def flowrate(self, axis=0):
+        return lbm_flowrate(self.h, axis)
+
+    def totals(self):
+        return lbm_totals(self.h)
+
+    def residual(self):
+        return lbm_residual(self.h)
+
+    def set_populations(self, f):
+        lbm_set_populations(self.h, f)
+
+    def get_populations(self):
+        return lbm_get_populations(self.h)
+
+    def set_tau(self, t):
+        lbm_set_tau(self.h, t)
+
+    def get_tau(self):
+        return lbm_get_tau(self.h)
+
+    @property
+    def steps_done(self):
+        return lbm_get_info(self.h).steps_done
+
+    def close(self):
+        if getattr(self, "h", None):
+            lbm_destroy(self.h)
+            self.h = None
+        self._ws = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

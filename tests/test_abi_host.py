@@ -1,0 +1,132 @@
+"""Host-side checks of the C ABI (no GPU needed): the library builds, loads and
+exports every symbol include/bingham_lbm.h declares; the GPU path's own
+velocity tables satisfy the lattice identities; argument validation rejects
+bad input before any CUDA call."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1610_01388_gb300 import _build
+from paper_1610_01388_gb300 import lbm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    _build.build()
+    yield
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "bingham_lbm.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbm_[a-z_]+)\s*\(", txt)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = lbm.library()
+    names = _declared()
+    assert len(names) >= 18
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(lbm.EXPORTED) <= set(names)
+
+
+LATS = {"D2Q9": (9, 2), "D3Q15": (15, 3), "D3Q19": (19, 3), "D3Q27": (27, 3)}
+
+
+@pytest.mark.parametrize("lat", list(LATS))
+def test_gpu_lattice_tables(lat):
+    c, w = lbm.lbm_lattice_info(lat)
+    Q, D = LATS[lat]
+    assert c.shape == (Q, 3)
+    assert len({tuple(v) for v in c}) == Q
+    assert tuple(c[0]) == (0, 0, 0)
+    for i in range(1, Q, 2):          # opposite pairs are adjacent
+        assert np.array_equal(c[i + 1], -c[i]) and w[i] == w[i + 1]
+    cf = c.astype(np.float64)
+    d = np.zeros((3, 3))
+    d[:D, :D] = np.eye(D)
+    assert abs(w.sum() - 1) < 1e-15
+    assert np.allclose(cf.T @ w, 0)
+    assert np.allclose(np.einsum("i,ia,ib->ab", w, cf, cf), d / 3, atol=1e-16)
+    m4 = np.einsum("i,ia,ib,ic,id->abcd", w, cf, cf, cf, cf)
+    iso = (np.einsum("ab,cd->abcd", d, d) + np.einsum("ac,bd->abcd", d, d)
+           + np.einsum("ad,bc->abcd", d, d)) / 9
+    assert np.allclose(m4, iso, atol=1e-16)
+
+
+def test_params_default():
+    p = lbm.lbm_params_default()
+    assert p.model == lbm.LBM_MODEL_IR and p.storage == lbm.LBM_F32
+    assert p.mu_p == 0.1 and p.gammadot_c == 1e-8 and p.magic == 0.25 and p.check_every == 0
+
+
+def _create_status(lat, mask, **kw):
+    lib = lbm.library()
+    p = lbm.lbm_params_default(**kw)
+    mask = np.ascontiguousarray(mask, np.uint8)
+    if mask.ndim == 2:
+        mask = mask[None]
+    nz, ny, nx = mask.shape
+    h = ctypes.c_void_p()
+    st = lib.lbm_create(ctypes.byref(h), lbm.LATTICES[lat], nx, ny, nz,
+                        ctypes.c_void_p(mask.ctypes.data), ctypes.byref(p), None)
+    if st == lbm.LBM_OK:
+        lib.lbm_destroy(h)
+    return st, lib.lbm_last_error().decode()
+
+
+@pytest.mark.parametrize("lat,mask,kw,expect", [
+    ("D2Q9", np.zeros((2, 4, 4)), {}, "nz == 1"),
+    ("D3Q19", np.ones((2, 2, 2)), {}, "no fluid"),
+    ("D3Q19", np.zeros((2, 2, 2)), {"mu_p": 0.0}, "mu_p"),
+    ("D3Q19", np.zeros((2, 2, 2)), {"mu_p": float("nan")}, "mu_p"),
+    ("D3Q19", np.zeros((2, 2, 2)), {"sigma_y": -1.0}, "sigma_y"),
+    ("D3Q19", np.zeros((2, 2, 2)), {"model": "PR", "gammadot_c": 0.0}, "gammadot_c"),
+    ("D3Q19", np.zeros((2, 2, 2)), {"model": "PR", "m": -1.0}, "m must"),
+    ("D3Q19", np.zeros((2, 2, 2)), {"model": "PR", "magic": 0.0}, "magic"),
+    ("D2Q9", np.zeros((1, 4, 4)), {"g": (0, 0, 1e-6)}, "g[2]"),
+    ("D3Q19", np.zeros((2, 2, 2)), {"check_every": -1}, "check_every"),
+    ("D3Q19", np.zeros((2, 2, 2)), {"flags": 0x80}, "flags"),
+])
+def test_create_rejects_invalid_arguments(lat, mask, kw, expect):
+    st, msg = _create_status(lat, mask, **kw)
+    assert st == lbm.LBM_EINVAL
+    assert expect in msg
+
+
+def test_create_rejects_empty_and_oversized_extents():
+    lib = lbm.library()
+    p = lbm.lbm_params_default()
+    h = ctypes.c_void_p()
+    m = np.zeros(1, np.uint8)
+    assert lib.lbm_create(ctypes.byref(h), 1, 0, 1, 1, ctypes.c_void_p(m.ctypes.data),
+                          ctypes.byref(p), None) == lbm.LBM_EINVAL
+    b = ctypes.c_size_t()
+    assert lib.lbm_workspace_bytes(3, 2048, 2048, 1024, ctypes.byref(p),
+                                   ctypes.byref(b)) == lbm.LBM_EINVAL
+    assert lib.lbm_create(ctypes.byref(h), 1, 4, 4, 4, None, ctypes.byref(p),
+                          None) == lbm.LBM_EINVAL
+
+
+def test_workspace_bytes_cover_the_layout():
+    p = lbm.lbm_params_default(model="PR", check_every=10)
+    n = lbm.lbm_workspace_bytes("D3Q27", 256, 128, 128, p)
+    cells = 256 * 128 * 128
+    # two population buffers, links, tau, 3-component snapshot, mask
+    assert n >= 2 * 27 * 4 * cells + 4 * cells + 4 * cells + 12 * cells + cells
+    p64 = lbm.lbm_params_default(model="IR", storage="F64")
+    assert lbm.lbm_workspace_bytes("D3Q27", 256, 128, 128, p64) >= 2 * 27 * 8 * cells
+
+
+def test_null_handle_is_rejected():
+    lib = lbm.library()
+    assert lib.lbm_step(None, 1) == lbm.LBM_EINVAL
+    assert lib.lbm_sync(None) == lbm.LBM_EINVAL
+    lib.lbm_destroy(None)   # no-op
+    assert lib.lbm_status_string(lbm.LBM_ECUDA) == b"CUDA error"

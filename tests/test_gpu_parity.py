@@ -1,0 +1,220 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Bars: FP64 storage agrees to round-off (1e-12 relative); FP32 storage has a
+relative L2 velocity error <= 1e-5 against the oracle at equal step count,
+and single collisions agree to 1e-5 of the non-equilibrium scale.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1610_01388_gb300 import lbm
+from paper_1610_01388_gb300 import workloads as W
+
+from _pairs import LAT_Q, gpu_to_oracle, make_pair, oracle_to_gpu, rel_l2_u, set_both
+
+pytestmark = pytest.mark.gpu
+
+LATS = ["D2Q9", "D3Q15", "D3Q19", "D3Q27"]
+TOL = {"F64": 1e-12, "F32": 1e-5}
+
+
+def _g(lat, scale=1e-5):
+    return (scale, -0.3 * scale, 0.0 if lat == "D2Q9" else 0.2 * scale)
+
+
+# --- single-cell brute force -------------------------------------------------
+
+@pytest.mark.parametrize("lat", LATS)
+@pytest.mark.parametrize("model", ["PR", "IR"])
+@pytest.mark.parametrize("storage", ["F64", "F32"])
+def test_single_cell_collision(lat, model, storage):
+    """A 1-cell periodic domain streams every population back into its own
+    cell, so one step is one collision; compare with the oracle's direct
+    per-population sums over several seeded states and parameter sets."""
+    mask = np.zeros((1, 1, 1), np.uint8)
+    _, w_orc, _ = oracle.lattice_info(lat)
+    cases = [dict(nu_p=0.1, sigma_y=0.0, m=0.0), dict(nu_p=0.05, sigma_y=2e-4, m=1e4),
+             dict(nu_p=0.3, sigma_y=5e-3, m=1e8), dict(nu_p=0.02, sigma_y=1e-5, m=1e6)]
+    for k, prm in enumerate(cases):
+        s, o = make_pair(lat, mask, model=model, storage=storage, g=_g(lat, 3e-5), **prm)
+        f0 = W.random_populations(w_orc, 1, amplitude=0.02, seed=100 + k)
+        tau0 = np.array([0.5 + 3 * (prm["nu_p"] + 0.7 * prm["m"] * prm["sigma_y"]) + 0.05])
+        set_both(lat, s, o, f0, tau=tau0 if model == "PR" else None)
+        s.step(1)
+        o.step(1)
+        fg = gpu_to_oracle(lat, s.get_populations())
+        scale = np.max(np.abs(o.f - w_orc[:, None]))
+        err = np.max(np.abs(fg - o.f)) / scale
+        assert err < (1e-12 if storage == "F64" else 1e-5), (prm, err)
+        if model == "PR":
+            tg = s.get_tau().reshape(-1)
+            assert abs(tg[0] - o.tau[0]) / o.tau[0] < (1e-12 if storage == "F64" else 1e-5)
+        s.close()
+
+
+# --- small domains, many steps -------------------------------------------------
+
+@pytest.mark.parametrize("model", ["PR", "IR"])
+@pytest.mark.parametrize("storage", ["F64", "F32"])
+def test_channel_d2q9(model, storage):
+    prm = W.channel_params(H=63, nu_p=0.1, u_newton=0.01, bn=1.0)
+    s, o = make_pair("D2Q9", W.channel_mask(4, 64), model=model, storage=storage,
+                     sigma_y=prm["sigma_y"], m=1e4, g=(prm["g"], 0, 0))
+    s.step(2000)
+    o.step(2000)
+    assert rel_l2_u(s, o) < TOL[storage]
+    s.close()
+
+
+@pytest.mark.parametrize("lat", ["D3Q15", "D3Q19", "D3Q27"])
+@pytest.mark.parametrize("model", ["PR", "IR"])
+def test_ragged_duct_random_start(lat, model):
+    """37 x 21 x 19 duct (58 blocks of 256 with a ragged tail), seeded random
+    start so every bounce-back link carries data, FP32, 120 steps."""
+    mask = W.duct_mask(37, 21, 19)
+    s, o = make_pair(lat, mask, model=model, storage="F32", sigma_y=2e-5, m=1e5,
+                     g=(2e-5, 0, 0), nu_p=0.08)
+    f0 = W.random_populations(o.w, o.N, amplitude=0.01, seed=7)
+    set_both(lat, s, o, f0)
+    s.step(120)
+    o.step(120)
+    assert rel_l2_u(s, o) < 1e-5
+    s.close()
+
+
+@pytest.mark.parametrize("model", ["PR", "IR"])
+def test_porous_d3q19(model):
+    mask, info = W.porous_mask(40, porosity=0.7, r_min=4, r_max=6, seed=2)
+    s, o = make_pair("D3Q19", mask, model=model, storage="F32", sigma_y=1e-5, m=1e5,
+                     g=(1e-5, 0, 0), nu_p=0.1)
+    s.step(200)
+    o.step(200)
+    assert rel_l2_u(s, o) < 1e-5
+    assert abs(s.flowrate(0) - o.flowrate(0)) < 1e-5 * abs(o.flowrate(0))
+    s.close()
+
+
+@pytest.mark.parametrize("lat", LATS)
+def test_fp64_storage_matches_to_roundoff(lat):
+    shape = (1, 9, 7) if lat == "D2Q9" else (5, 6, 7)
+    mask = np.zeros(shape, np.uint8)
+    mask[..., 0, :] = 1
+    for model in ("PR", "IR"):
+        s, o = make_pair(lat, mask, model=model, storage="F64", sigma_y=3e-5, m=1e6,
+                         g=_g(lat, 1e-5))
+        set_both(lat, s, o, W.random_populations(o.w, o.N, amplitude=0.02, seed=3))
+        s.step(50)
+        o.step(50)
+        fg = gpu_to_oracle(lat, s.get_populations())
+        fl = mask.reshape(-1) == 0
+        assert np.max(np.abs(fg[:, fl] - o.f[:, fl])) < 1e-13
+        s.close()
+
+
+# --- edge cases ---------------------------------------------------------------
+
+@pytest.mark.parametrize("lat,shape", [("D3Q19", (7, 5, 1)), ("D3Q27", (1, 1, 6)),
+                                       ("D3Q15", (3, 1, 2)), ("D2Q9", (1, 1, 5))])
+def test_degenerate_extents(lat, shape):
+    """Extents of 1 (every neighbour in that axis is the cell itself)."""
+    mask = np.zeros(shape, np.uint8)
+    s, o = make_pair(lat, mask, model="IR", storage="F64", sigma_y=1e-5, g=_g(lat))
+    set_both(lat, s, o, W.random_populations(o.w, o.N, amplitude=0.02, seed=5))
+    s.step(10)
+    o.step(10)
+    assert np.max(np.abs(gpu_to_oracle(lat, s.get_populations()) - o.f)) < 1e-13
+    s.close()
+
+
+def test_isolated_cell_and_solid_neighbourhood():
+    """A fluid cell boxed in by solids bounces every population back."""
+    mask = np.ones((3, 3, 3), np.uint8)
+    mask[1, 1, 1] = 0
+    s, o = make_pair("D3Q27", mask, model="PR", storage="F64", sigma_y=1e-4, m=1e4)
+    set_both("D3Q27", s, o, W.random_populations(o.w, o.N, amplitude=0.02, seed=9))
+    s.step(5)
+    o.step(5)
+    c = 13   # cell (1,1,1)
+    assert np.max(np.abs(gpu_to_oracle("D3Q27", s.get_populations())[:, c] - o.f[:, c])) < 1e-13
+    s.close()
+
+
+@pytest.mark.parametrize("model", ["PR", "IR"])
+def test_momentum_balance_wall_less(model):
+    """No walls: total momentum gains exactly n g M (FP64 storage)."""
+    mask = np.zeros((6, 5, 8), np.uint8)
+    g = (2e-5, -1e-5, 5e-6)
+    s, o = make_pair("D3Q19", mask, model=model, storage="F64", sigma_y=1e-5, m=1e5, g=g)
+    set_both("D3Q19", s, o, W.random_populations(o.w, o.N, amplitude=0.02, seed=2))
+    M0, P0 = s.totals()
+    s.step(40)
+    M1, P1 = s.totals()
+    assert abs(M1 - M0) < 1e-12 * M0
+    assert np.allclose(P1 - P0, 40 * M0 * np.array(g), rtol=1e-10, atol=1e-14)
+    s.close()
+
+
+def test_graph_replay_is_bitwise_identical_to_single_launches():
+    mask = W.duct_mask(16, 12, 10)
+    a, _ = make_pair("D3Q27", mask, model="PR", sigma_y=1e-5, m=1e5, g=(1e-5, 0, 0))
+    b, _ = make_pair("D3Q27", mask, model="PR", sigma_y=1e-5, m=1e5, g=(1e-5, 0, 0))
+    a.step(201)                 # uses 64-step CUDA graphs for 192 of them
+    for _ in range(201):
+        b.step(1)
+    assert np.array_equal(a.get_populations(), b.get_populations())
+    assert np.array_equal(a.get_tau(), b.get_tau())
+    a.close()
+    b.close()
+
+
+def test_torch_workspace_matches_library_allocation():
+    import torch
+    mask = W.duct_mask(20, 10, 9)
+    a, _ = make_pair("D3Q19", mask, model="IR", sigma_y=1e-5, g=(1e-5, 0, 0))
+    b, _ = make_pair("D3Q19", mask, model="IR", sigma_y=1e-5, g=(1e-5, 0, 0), use_torch=True)
+    a.step(100)
+    b.step(100)
+    torch.cuda.synchronize()
+    assert np.array_equal(a.get_populations(), b.get_populations())
+    a.close()
+    b.close()
+
+
+# --- diagnostics ----------------------------------------------------------------
+
+@pytest.mark.parametrize("model", ["PR", "IR"])
+def test_check_step_residual_and_flowrate(model):
+    mask = W.duct_mask(12, 17, 15)
+    k = 25
+    s, o = make_pair("D3Q27", mask, model=model, storage="F64", sigma_y=1e-5, m=1e5,
+                     g=(1e-5, 0, 0), check_every=k)
+    s.step(2 * k)
+    # the check step k computes the fields of the state it streams from,
+    # i.e. after k - 1 completed steps
+    o.step(k - 1)
+    _, u1 = o.fields()
+    o.step(k)
+    _, u2 = o.fields()
+    fl = mask == 0
+    r_orc = oracle.residual(u2, u1, fl)
+    r, at, qx = s.residual()
+    assert at == 2 * k
+    assert abs(r - r_orc) < 1e-10 * r_orc
+    assert abs(qx - np.sum(u2[0][fl]) / mask.shape[2]) < 1e-12 * abs(qx)
+    o.step(1)
+    assert abs(s.flowrate(0) - o.flowrate(0)) < 1e-12 * abs(o.flowrate(0))
+    s.close()
+
+
+def test_nonfinite_density_is_reported():
+    mask = W.duct_mask(8, 6, 6)
+    s, o = make_pair("D3Q19", mask, model="IR", storage="F32", check_every=1)
+    f = np.repeat(o.w[:, None], o.N, axis=1)
+    f[0, 8 * 6 + 9] = np.nan              # one fluid cell
+    s.set_populations(oracle_to_gpu("D3Q19", f))
+    s.step(1)
+    with pytest.raises(lbm.LbmError) as ei:
+        s.residual()
+    assert ei.value.status == lbm.LBM_ENONFINITE
+    s.close()
