@@ -370,6 +370,7 @@ def run_reference(args):
 
 
 def main(argv=None):
+    global NY, NZ
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2000)
@@ -383,7 +384,6 @@ def main(argv=None):
     ap.add_argument("--ny", type=int, default=NY, help="duct cross-section (profiling runs)")
     ap.add_argument("--nz", type=int, default=NZ)
     args = ap.parse_args(argv)
-    global NY, NZ
     NY, NZ = args.ny, args.nz
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -207,7 +207,9 @@ __device__ __forceinline__ void collide_ir(const Coef<R>& c, uint32_t flags, R (
     const R h0 = -(k1 * trT + k2 * R(L::D)) * third;
     const R uu = ux * ux + uy * uy + uz * uz;
     const R base = m.d - R(1.5) * rho * uu;
-    const R r45 = R(4.5) * rho, r3 = R(3) * rho;
+    const R r45 = R(4.5) * rho;
+    // odd part: w_i (3 rho c.u + 3/2 c.F) = 3 w_i c.(j + F), since rho u = j + F/2
+    const R qx = m.jx + Fx, qy = m.jy + Fy, qz = m.jz + Fz;
     f[0] = R(L::w(0)) * (base + R(4.5) * h0);
     static_for<0, (L::Q - 1) / 2>([&](auto P) {
         constexpr int i = 2 * decltype(P)::value + 1;
@@ -216,12 +218,12 @@ __device__ __forceinline__ void collide_ir(const Coef<R>& c, uint32_t flags, R (
         constexpr int c2 = cx * cx + cy * cy + cz * cz;
         const R w = R(L::w(i));
         const R cu = R(cx) * ux + R(cy) * uy + R(cz) * uz;
-        const R cF = R(cx) * Fx + R(cy) * Fy + R(cz) * Fz;
+        const R cq = R(cx) * qx + R(cy) * qy + R(cz) * qz;
         const R cTc = R(cx * cx) * T.xx + R(cy * cy) * T.yy + R(cz * cz) * T.zz +
                       R(2 * cx * cy) * T.xy + R(2 * cx * cz) * T.xz + R(2 * cy * cz) * T.yz;
         const R h = h0 + k1 * cTc + k2 * R(c2);
         const R e = w * (base + r45 * cu * cu + R(4.5) * h);
-        const R od = w * (r3 * cu + R(1.5) * cF);
+        const R od = odd_w<L, R>(i) * cq;
         f[i] = e + od;
         f[o] = e - od;
     });
@@ -265,7 +267,8 @@ __device__ __forceinline__ void collide_pr(const Coef<R>& c, uint32_t flags, R (
     const R gg = gx * gx + gy * gy + gz * gz;
     const R base = m.d - R(1.5) * rho * uu;                 // even part of f_eq - w, direction-free
     const R fbase = R(-1.5) * rho * (R(2) * ug + gg);      // even part of the EDM difference
-    const R r45 = R(4.5) * rho, r3 = R(3) * rho;
+    const R r45 = R(4.5) * rho;
+    const R Fx = rho * gx, Fy = rho * gy, Fz = rho * gz;
     {
         const R w0 = R(L::w(0));
         f[0] = f[0] - wp * (f[0] - w0 * base) + w0 * fbase;
@@ -275,14 +278,16 @@ __device__ __forceinline__ void collide_pr(const Coef<R>& c, uint32_t flags, R (
         constexpr int o = i + 1;
         constexpr int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
         const R w = R(L::w(i));
+        const R w3 = odd_w<L, R>(i);
         const R cu = R(cx) * ux + R(cy) * uy + R(cz) * uz;
         const R cg = R(cx) * gx + R(cy) * gy + R(cz) * gz;
         const R fe = R(0.5) * (f[i] + f[o]);
         const R fo = R(0.5) * (f[i] - f[o]);
         const R eqe = w * (base + r45 * cu * cu);
-        const R eqo = w * (r3 * cu);
+        // odd parts from j and F directly: 3 w_i rho c.u = 3 w_i c.j exactly
+        const R eqo = w3 * (R(cx) * m.jx + R(cy) * m.jy + R(cz) * m.jz);
         const R Fe = w * (fbase + r45 * cg * (R(2) * cu + cg));
-        const R Fo = w * (r3 * cg);
+        const R Fo = w3 * (R(cx) * Fx + R(cy) * Fy + R(cz) * Fz);
         const R E = fe - wp * (fe - eqe) + Fe;
         const R O = fo - wm * (fo - eqo) + Fo;
         f[i] = E + O;
