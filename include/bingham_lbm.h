@@ -184,6 +184,37 @@ typedef struct {
 } lbm_info;
 lbm_status lbm_get_info(const lbm_solver *s, lbm_info *info);
 
+/* Flow rate along `axis`, like lbm_flowrate, for callers that must not
+ * allocate memory at this point: code that runs under a fixed device-memory
+ * budget with every byte handed out up front (a serving loop admitting solves
+ * against a budget), code that shares the device through its own memory pool,
+ * or code in a latency-critical loop where cudaMalloc (which can synchronise
+ * the device and can fail under memory pressure) is not acceptable.
+ * The paper has no counterpart; this is an interface convenience.
+ *
+ * It allocates nothing: no cudaMalloc, cudaFree, host or pinned allocation.
+ * Inputs are the solver's resident populations; the output is one double
+ * written to q_device, a caller-owned DEVICE pointer (8-byte aligned), as
+ * Q_a = (1/L_a) sum over fluid cells of u_real,a.  The work is enqueued on
+ * the solver's stream and the call returns without synchronising.
+ *
+ * Scratch: the per-block FP64 partial sums live in one file-scope device
+ * array of the library, 1216 blocks x 8 doubles (76 KiB), which every GPU
+ * that loads the library holds until the process exits.  The reduction is a
+ * grid-stride loop with at most 1216 blocks, so every domain lbm_create
+ * accepts fits; a launch that would need more partials is rejected with
+ * LBM_EINVAL.  Each call writes every partial it reads, so nothing has to be
+ * cleared between calls, but the array keeps the last call's contents and
+ * is shared by all solvers and threads: calls whose work overlaps on the GPU
+ * (different streams, or different host threads, without ordering) race on
+ * it.  Order such calls on one stream or synchronise between them.
+ *
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture on that device.  Axis outside 0..2, a NULL
+ * q_device or a poisoned handle are rejected before any GPU work. */
+lbm_status lbm_flowrate_noalloc(lbm_solver *s, int axis, double *q_device);
+
 /* Releases the handle and the device memory the library allocated. */
 void lbm_destroy(lbm_solver *s);
 

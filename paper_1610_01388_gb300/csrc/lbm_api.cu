@@ -14,6 +14,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -686,6 +687,85 @@ lbm_status lbm_get_info(const lbm_solver* s, lbm_info* info) {
                      (s->p.model == LBM_MODEL_PR ? 2.0 * arith_bytes(s->p.storage) : 0.0);
     info->bytes_per_fluid_update = b;
     info->device_bytes = s->lay.total;
+    return LBM_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free flow rate (lbm_flowrate_noalloc): the same grid-stride
+// reduction kernel as lbm_flowrate, with its block partials in a file-scope
+// device array instead of the solver's workspace.
+namespace {
+
+constexpr int kStaticParts = 1216;   // = the grid cap of reduce_grid()
+static __device__ __align__(256) double g_static_partials[kStaticParts * kNumStats];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+double* g_static_addr[kMaxDevices] = {nullptr};
+
+// Device address of g_static_partials on the current device, looked up once
+// per device (host code may not use the symbol itself as a device pointer).
+lbm_status static_partials(int dev, double** out) {
+    if (dev < 0 || dev >= kMaxDevices) return fail(LBM_EUNSUPPORTED, "device index %d out of range", dev);
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_addr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_static_partials);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(LBM_ECUDA, "cudaGetSymbolAddress of the static reduction scratch: %s",
+                        cudaGetErrorString(e));
+        }
+        g_static_addr[dev] = (double*)p;
+    }
+    *out = g_static_addr[dev];
+    return LBM_OK;
+}
+
+// Fixed-order sum of the partials (one block) and Q_a = sum / L_a.
+__global__ void k_finalize_axis(int nparts, int slot, double inv_len, double* __restrict__ q) {
+    __shared__ double sm[kBlock];
+    double v = 0.0;
+    for (int b = threadIdx.x; b < nparts; b += kBlock) v += g_static_partials[b * kNumStats + slot];
+    sm[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = kBlock / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *q = sm[0] * inv_len;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_flowrate_noalloc(lbm_solver* s, int axis, double* q_device) {
+    lbm_status v = enter(s);
+    if (v != LBM_OK) return v;
+    if (axis < 0 || axis > 2) return fail(LBM_EINVAL, "axis must be 0, 1 or 2");
+    if (!q_device) return fail(LBM_EINVAL, "q_device is NULL");
+    if (((uintptr_t)q_device & 7u) != 0) return fail(LBM_EINVAL, "q_device must be 8-byte aligned");
+    const int nb = reduce_grid(s->ncells);
+    if (nb > kStaticParts)
+        return fail(LBM_EINVAL, "reduction needs %d partial blocks, the static scratch holds %d",
+                    nb, kStaticParts);
+    double* parts = nullptr;
+    if ((v = static_partials(s->device, &parts)) != LBM_OK) return v;
+    const void* f = s->f[s->cur];
+    cudaError_t e;
+    switch (s->lat) {
+    case LBM_D2Q9: e = launch_reduce_D2Q9(s->p.storage, kReduceFlow, s->kp, f, s->links, parts, nb, s->stream); break;
+    case LBM_D3Q15: e = launch_reduce_D3Q15(s->p.storage, kReduceFlow, s->kp, f, s->links, parts, nb, s->stream); break;
+    case LBM_D3Q19: e = launch_reduce_D3Q19(s->p.storage, kReduceFlow, s->kp, f, s->links, parts, nb, s->stream); break;
+    default: e = launch_reduce_D3Q27(s->p.storage, kReduceFlow, s->kp, f, s->links, parts, nb, s->stream); break;
+    }
+    CK(s, e, "static-scratch reduction kernel");
+    const int L = axis == 0 ? s->nx : (axis == 1 ? s->ny : s->nz);
+    k_finalize_axis<<<1, kBlock, 0, s->stream>>>(nb, kStatUx + axis, 1.0 / L, q_device);
+    CK(s, cudaGetLastError(), "static-scratch finalize kernel");
     return LBM_OK;
 }
 

@@ -96,6 +96,7 @@ def library():
             "lbm_set_tau": [vp, vp],
             "lbm_get_tau": [vp, vp],
             "lbm_get_info": [vp, P(lbm_info)],
+            "lbm_flowrate_noalloc": [vp, i32, vp],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
@@ -212,6 +213,12 @@ def lbm_flowrate(h, axis=0) -> float:
     q = ctypes.c_double()
     _check(library().lbm_flowrate(h, int(axis), ctypes.byref(q)))
     return q.value
+
+
+def lbm_flowrate_noalloc(h, axis, q_device_ptr):
+    """Flow rate written to a caller-owned device double; allocates nothing and
+    does not synchronise (see the header for the shared static scratch)."""
+    _check(library().lbm_flowrate_noalloc(h, int(axis), ctypes.c_void_p(q_device_ptr)))
 
 
 def lbm_totals(h):
