@@ -47,6 +47,45 @@ __device__ __forceinline__ void static_for(F&& f) {
     }
 }
 
+// Sums with compile-time integer coefficients.  Terms with a zero
+// coefficient are left out entirely (IEEE arithmetic forbids the compiler to
+// drop 0 * x or x + 0 by itself), +-1 become adds and subtracts.
+template <class R, bool Started> struct CSum {
+    R v;
+};
+
+template <int c, class R, bool S>
+__device__ __forceinline__ auto cadd(CSum<R, S> a, R x) {
+    if constexpr (c == 0) {
+        return a;
+    } else if constexpr (!S) {
+        if constexpr (c == 1) return CSum<R, true>{x};
+        else if constexpr (c == -1) return CSum<R, true>{-x};
+        else return CSum<R, true>{R(c) * x};
+    } else {
+        if constexpr (c == 1) return CSum<R, true>{a.v + x};
+        else if constexpr (c == -1) return CSum<R, true>{a.v - x};
+        else return CSum<R, true>{a.v + R(c) * x};
+    }
+}
+
+template <class R, bool S> __device__ __forceinline__ R cval(CSum<R, S> a) {
+    if constexpr (S) return a.v;
+    else return R(0);
+}
+
+// a x + b y + c z
+template <int a, int b, int c, class R>
+__device__ __forceinline__ R cdot(R x, R y, R z) {
+    return cval(cadd<c>(cadd<b>(cadd<a>(CSum<R, false>{R(0)}, x), y), z));
+}
+
+// a x + b y + c z + d p + e q + g r
+template <int a, int b, int c, int d, int e, int g, class R>
+__device__ __forceinline__ R cdot6(R x, R y, R z, R p, R q, R r) {
+    return cval(cadd<g>(cadd<e>(cadd<d>(cadd<c>(cadd<b>(cadd<a>(CSum<R, false>{R(0)}, x), y), z), p), q), r));
+}
+
 // ---------------------------------------------------------------------------
 // storage
 template <class S> struct Store;
@@ -100,7 +139,8 @@ __device__ __forceinline__ void gather(const KParams& kp, const S* __restrict__ 
     const int dzm = (z == 0) ? (nz - 1) * sz : -sz;
     const int dzp = (z == nz - 1) ? -(nz - 1) * sz : sz;
     const int64_t plane = kp.plane;
-    static_for<0, L::Q>([&](auto I) {
+    const S* __restrict__ base = f + idx;
+    auto offset = [&](auto I) {
         constexpr int i = decltype(I)::value;
         constexpr int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
         int off = 0;
@@ -110,10 +150,22 @@ __device__ __forceinline__ void gather(const KParams& kp, const S* __restrict__ 
         if constexpr (cy < 0) off += dyp;
         if constexpr (cz > 0) off += dzm;
         if constexpr (cz < 0) off += dzp;
-        const S* p = ((lk >> i) & 1u) ? (f + (int64_t)L::opp(i) * plane + idx)
-                                      : (f + (int64_t)i * plane + (idx + off));
-        v[i] = Store<S>::ld(p);
-    });
+        return off;
+    };
+    if (lk == 0u) {
+        // no solid neighbour: plain pull, no per-population selects
+        static_for<0, L::Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            v[i] = Store<S>::ld(base + ((int64_t)i * plane + offset(I)));
+        });
+    } else {
+        static_for<0, L::Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            const S* p = ((lk >> i) & 1u) ? (base + (int64_t)L::opp(i) * plane)
+                                          : (base + ((int64_t)i * plane + offset(I)));
+            v[i] = Store<S>::ld(p);
+        });
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -122,48 +174,69 @@ template <class R> struct Mom {
     R d, jx, jy, jz, xx, yy, zz, xy, xz, yz;
 };
 
+// Grouped sums: populations are added once per velocity class (c_x = +1, -1,
+// 0; c_y = +-1; c_z = +-1; sign of c_x c_y, c_x c_z, c_y c_z) and the moments
+// are sums and differences of those class sums.  Accumulators start at -0.0,
+// the additive identity the compiler may drop.
 template <class L, class R>
 __device__ __forceinline__ Mom<R> moments(const R (&f)[L::Q]) {
-    Mom<R> m{R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
+    const R z0 = R(-0.0);
+    R xp = z0, xm = z0, x0 = z0, yp = z0, ym = z0, zp = z0, zm = z0;
+    R pxy = z0, mxy = z0, pxz = z0, mxz = z0, pyz = z0, myz = z0;
     static_for<0, L::Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
         constexpr int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
         const R v = f[i];
-        m.d += v;
-        if constexpr (cx == 1) m.jx += v;
-        if constexpr (cx == -1) m.jx -= v;
-        if constexpr (cy == 1) m.jy += v;
-        if constexpr (cy == -1) m.jy -= v;
-        if constexpr (cz == 1) m.jz += v;
-        if constexpr (cz == -1) m.jz -= v;
-        if constexpr (cx != 0) m.xx += v;
-        if constexpr (cy != 0) m.yy += v;
-        if constexpr (cz != 0) m.zz += v;
-        if constexpr (cx * cy == 1) m.xy += v;
-        if constexpr (cx * cy == -1) m.xy -= v;
-        if constexpr (cx * cz == 1) m.xz += v;
-        if constexpr (cx * cz == -1) m.xz -= v;
-        if constexpr (cy * cz == 1) m.yz += v;
-        if constexpr (cy * cz == -1) m.yz -= v;
+        if constexpr (cx == 1) xp += v;
+        else if constexpr (cx == -1) xm += v;
+        else x0 += v;
+        if constexpr (cy == 1) yp += v;
+        else if constexpr (cy == -1) ym += v;
+        if constexpr (cz == 1) zp += v;
+        else if constexpr (cz == -1) zm += v;
+        if constexpr (cx * cy == 1) pxy += v;
+        else if constexpr (cx * cy == -1) mxy += v;
+        if constexpr (cx * cz == 1) pxz += v;
+        else if constexpr (cx * cz == -1) mxz += v;
+        if constexpr (cy * cz == 1) pyz += v;
+        else if constexpr (cy * cz == -1) myz += v;
     });
+    Mom<R> m;
+    m.xx = xp + xm;
+    m.jx = xp - xm;
+    m.d = m.xx + x0;
+    m.yy = yp + ym;
+    m.jy = yp - ym;
+    m.xy = pxy - mxy;
+    if constexpr (L::D == 3) {
+        m.zz = zp + zm;
+        m.jz = zp - zm;
+        m.xz = pxz - mxz;
+        m.yz = pyz - myz;
+    } else {
+        m.zz = R(0);
+        m.jz = R(0);
+        m.xz = R(0);
+        m.yz = R(0);
+    }
     return m;
 }
 
 // Non-equilibrium second moment T = Pi - rho c_s^2 I - rho u u written with
 // offsets: Pi = c_s^2 I + p, rho = 1 + d.
-template <class L, class R> struct Tens {
+template <class R> struct Tens {
     R xx, yy, zz, xy, xz, yz;
 };
 
 template <class L, class R>
-__device__ __forceinline__ Tens<L, R> noneq(const Mom<R>& m, R rho, R ux, R uy, R uz, uint32_t flags) {
-    const R third = R(1.0 / 3.0);
-    Tens<L, R> t;
-    t.xx = m.xx - m.d * third - rho * ux * ux;
-    t.yy = m.yy - m.d * third - rho * uy * uy;
+__device__ __forceinline__ Tens<R> noneq(const Mom<R>& m, R rho, R ux, R uy, R uz, uint32_t flags) {
+    const R d3 = m.d * R(1.0 / 3.0);
+    Tens<R> t;
+    t.xx = m.xx - d3 - rho * ux * ux;
+    t.yy = m.yy - d3 - rho * uy * uy;
     t.xy = m.xy - rho * ux * uy;
     if constexpr (L::D == 3) {
-        t.zz = m.zz - m.d * third - rho * uz * uz;
+        t.zz = m.zz - d3 - rho * uz * uz;
         t.xz = m.xz - rho * ux * uz;
         t.yz = m.yz - rho * uy * uz;
     } else {
@@ -173,6 +246,19 @@ __device__ __forceinline__ Tens<L, R> noneq(const Mom<R>& m, R rho, R ux, R uy, 
     }
     if (flags & LBM_FLAG_BURNETT_X) t.xx = R(0);
     return t;
+}
+
+template <class L, class R> __device__ __forceinline__ R tnorm2(const Tens<R>& T) {
+    R s = T.xx * T.xx + T.yy * T.yy + R(2) * T.xy * T.xy;
+    if constexpr (L::D == 3) s += T.zz * T.zz + R(2) * (T.xz * T.xz + T.yz * T.yz);
+    return s;
+}
+
+// c.T.c for a lattice velocity, from T and the doubled off-diagonals
+template <int cx, int cy, int cz, class R>
+__device__ __forceinline__ R ctc(const Tens<R>& T, R t2xy, R t2xz, R t2yz) {
+    return cdot6<cx * cx, cy * cy, cz * cz, cx * cy, cx * cz, cy * cz>(T.xx, T.yy, T.zz, t2xy,
+                                                                        t2xz, t2yz);
 }
 
 // ---------------------------------------------------------------------------
@@ -187,10 +273,8 @@ __device__ __forceinline__ void collide_ir(const Coef<R>& c, uint32_t flags, R (
     const R ux = (m.jx + R(0.5) * Fx) * inv;
     const R uy = (m.jy + R(0.5) * Fy) * inv;
     const R uz = (L::D == 3) ? (m.jz + R(0.5) * Fz) * inv : R(0);
-    const Tens<L, R> T = noneq<L, R>(m, rho, ux, uy, uz, flags);
-    const R tn2 = T.xx * T.xx + T.yy * T.yy + T.zz * T.zz +
-                  R(2) * (T.xy * T.xy + T.xz * T.xz + T.yz * T.yz);
-    const R tn = sqrt(tn2);
+    const Tens<R> T = noneq<L, R>(m, rho, ux, uy, uz, flags);
+    const R tn = sqrt(tnorm2<L, R>(T));
     // s = as T, sigma = asg T  (eq. Vikh_sigmaS_tensor)
     R as = R(0), asg = R(-1);
     if (tn > R(0) && tn >= c.s2y) {
@@ -199,15 +283,16 @@ __device__ __forceinline__ void collide_ir(const Coef<R>& c, uint32_t flags, R (
         asg = -(c.six_nu * tn + c.s2y) * c.ir_b * it;
     }
     // A = -sigma_bar + s/2 = k1 T + k2 I with sigma_bar = sigma - tr(sigma)/D I
-    const R third = R(1.0 / 3.0);
     const R trT = T.xx + T.yy + T.zz;
     const R k1 = R(0.5) * as - asg;
     const R k2 = asg * trT * R(1.0 / L::D);
     // (c c - c_s^2 I):A = k1 (cTc - trT/3) + k2 (|c|^2 - D/3) = h0 + k1 cTc + k2 |c|^2
-    const R h0 = -(k1 * trT + k2 * R(L::D)) * third;
+    const R h0 = -(k1 * trT + k2 * R(L::D)) * R(1.0 / 3.0);
     const R uu = ux * ux + uy * uy + uz * uz;
     const R base = m.d - R(1.5) * rho * uu;
     const R r45 = R(4.5) * rho;
+    const R k145 = R(4.5) * k1;
+    const R t2xy = R(2) * T.xy, t2xz = R(2) * T.xz, t2yz = R(2) * T.yz;
     // odd part: w_i (3 rho c.u + 3/2 c.F) = 3 w_i c.(j + F), since rho u = j + F/2
     const R qx = m.jx + Fx, qy = m.jy + Fy, qz = m.jz + Fz;
     f[0] = R(L::w(0)) * (base + R(4.5) * h0);
@@ -217,13 +302,13 @@ __device__ __forceinline__ void collide_ir(const Coef<R>& c, uint32_t flags, R (
         constexpr int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
         constexpr int c2 = cx * cx + cy * cy + cz * cz;
         const R w = R(L::w(i));
-        const R cu = R(cx) * ux + R(cy) * uy + R(cz) * uz;
-        const R cq = R(cx) * qx + R(cy) * qy + R(cz) * qz;
-        const R cTc = R(cx * cx) * T.xx + R(cy * cy) * T.yy + R(cz * cz) * T.zz +
-                      R(2 * cx * cy) * T.xy + R(2 * cx * cz) * T.xz + R(2 * cy * cz) * T.yz;
-        const R h = h0 + k1 * cTc + k2 * R(c2);
-        const R e = w * (base + r45 * cu * cu + R(4.5) * h);
-        const R od = odd_w<L, R>(i) * cq;
+        // even part e = w (base + 4.5 rho cu^2 + 4.5 h) = A + B cu^2 + C cTc (per class A, B, C)
+        const R A = w * (base + R(4.5) * (h0 + k2 * R(c2)));
+        const R B = w * r45;
+        const R C = w * k145;
+        const R cu = cdot<cx, cy, cz>(ux, uy, uz);
+        const R e = A + B * (cu * cu) + C * ctc<cx, cy, cz>(T, t2xy, t2xz, t2yz);
+        const R od = odd_w<L, R>(i) * cdot<cx, cy, cz>(qx, qy, qz);
         f[i] = e + od;
         f[o] = e - od;
     });
@@ -243,11 +328,9 @@ __device__ __forceinline__ void collide_pr(const Coef<R>& c, uint32_t flags, R (
     const R rho = R(1) + m.d;
     const R inv = R(1) / rho;
     const R ux = m.jx * inv, uy = m.jy * inv, uz = (L::D == 3) ? m.jz * inv : R(0);
-    const Tens<L, R> T = noneq<L, R>(m, rho, ux, uy, uz, flags);
-    const R tn2 = T.xx * T.xx + T.yy * T.yy + T.zz * T.zz +
-                  R(2) * (T.xy * T.xy + T.xz * T.xz + T.yz * T.yz);
+    const Tens<R> T = noneq<L, R>(m, rho, ux, uy, uz, flags);
     // D = -T / (2 tau_old c_s^2) = -1.5 T / tau_old ; gdot = sqrt(2 D:D)
-    const R gd = R(1.5) / tau * sqrt(R(2) * tn2);
+    const R gd = R(1.5) / tau * sqrt(R(2) * tnorm2<L, R>(T));
     const R sy_rho = c.sigma_y * inv;
     R nu;
     if (gd >= c.gdot_c) {
@@ -262,13 +345,13 @@ __device__ __forceinline__ void collide_pr(const Coef<R>& c, uint32_t flags, R (
     const R wm = R(1) / (R(0.5) + c.magic / (tn - R(0.5)));
     tau = tn;
     const R gx = c.g[0], gy = c.g[1], gz = (L::D == 3) ? c.g[2] : R(0);
+    const R Fx = rho * gx, Fy = rho * gy, Fz = rho * gz;
     const R uu = ux * ux + uy * uy + uz * uz;
     const R ug = ux * gx + uy * gy + uz * gz;
     const R gg = gx * gx + gy * gy + gz * gz;
     const R base = m.d - R(1.5) * rho * uu;                 // even part of f_eq - w, direction-free
     const R fbase = R(-1.5) * rho * (R(2) * ug + gg);      // even part of the EDM difference
     const R r45 = R(4.5) * rho;
-    const R Fx = rho * gx, Fy = rho * gy, Fz = rho * gz;
     {
         const R w0 = R(L::w(0));
         f[0] = f[0] - wp * (f[0] - w0 * base) + w0 * fbase;
@@ -279,15 +362,16 @@ __device__ __forceinline__ void collide_pr(const Coef<R>& c, uint32_t flags, R (
         constexpr int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
         const R w = R(L::w(i));
         const R w3 = odd_w<L, R>(i);
-        const R cu = R(cx) * ux + R(cy) * uy + R(cz) * uz;
-        const R cg = R(cx) * gx + R(cy) * gy + R(cz) * gz;
+        const R cu = cdot<cx, cy, cz>(ux, uy, uz);
+        const R cg = cdot<cx, cy, cz>(gx, gy, gz);
         const R fe = R(0.5) * (f[i] + f[o]);
         const R fo = R(0.5) * (f[i] - f[o]);
-        const R eqe = w * (base + r45 * cu * cu);
+        const R wr = w * r45;
+        const R eqe = w * base + wr * (cu * cu);
         // odd parts from j and F directly: 3 w_i rho c.u = 3 w_i c.j exactly
-        const R eqo = w3 * (R(cx) * m.jx + R(cy) * m.jy + R(cz) * m.jz);
-        const R Fe = w * (fbase + r45 * cg * (R(2) * cu + cg));
-        const R Fo = w3 * (R(cx) * Fx + R(cy) * Fy + R(cz) * Fz);
+        const R eqo = w3 * cdot<cx, cy, cz>(m.jx, m.jy, m.jz);
+        const R Fe = w * fbase + wr * (cg * (R(2) * cu + cg));
+        const R Fo = w3 * cdot<cx, cy, cz>(Fx, Fy, Fz);
         const R E = fe - wp * (fe - eqe) + Fe;
         const R O = fo - wm * (fo - eqo) + Fo;
         f[i] = E + O;
@@ -300,8 +384,12 @@ __device__ __forceinline__ void collide_pr(const Coef<R>& c, uint32_t flags, R (
 }
 
 // ---------------------------------------------------------------------------
-// deterministic block reduction of kNumStats doubles (fixed shuffle tree)
-__device__ __forceinline__ void block_sum_store(double (&v)[kNumStats], double* __restrict__ out) {
+// deterministic block reduction of kNumStats values (fixed shuffle tree).
+// The warp stage runs in the type of v (the arithmetic type on check steps,
+// which keeps FP32 paths off the low-rate FP64 pipe); the sums across warps
+// and blocks are FP64.
+template <class V>
+__device__ __forceinline__ void block_sum_store(V (&v)[kNumStats], double* __restrict__ out) {
     __shared__ double sm[kBlock / 32][kNumStats];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -311,7 +399,7 @@ __device__ __forceinline__ void block_sum_store(double (&v)[kNumStats], double* 
     }
     if (lane == 0) {
 #pragma unroll
-        for (int k = 0; k < kNumStats; ++k) sm[warp][k] = v[k];
+        for (int k = 0; k < kNumStats; ++k) sm[warp][k] = (double)v[k];
     }
     __syncthreads();
     if (warp == 0) {
@@ -319,7 +407,7 @@ __device__ __forceinline__ void block_sum_store(double (&v)[kNumStats], double* 
         for (int k = 0; k < kNumStats; ++k) {
             double t = (lane < kBlock / 32) ? sm[lane][k] : 0.0;
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+            for (int o = 4; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
             if (lane == 0) out[k] = t;
         }
     }
@@ -341,10 +429,10 @@ k_step(const KArgs a, const S* __restrict__ fsrc, S* __restrict__ fdst,
     if constexpr (!CHECK) {
         if (!active) return;
     }
-    double acc[kNumStats];
+    R acc[kNumStats];
     if constexpr (CHECK) {
 #pragma unroll
-        for (int k = 0; k < kNumStats; ++k) acc[k] = 0.0;
+        for (int k = 0; k < kNumStats; ++k) acc[k] = R(0);
     }
     if (active) {
         R f[L::Q];
@@ -358,23 +446,25 @@ k_step(const KArgs a, const S* __restrict__ fsrc, S* __restrict__ fdst,
             collide_ir<L, R>(coef<R>(a), kp.flags, f, drho, ur);
         }
         const int64_t plane = kp.plane;
-#pragma unroll
-        for (int i = 0; i < L::Q; ++i) Store<S>::st(fdst + (int64_t)i * plane + idx, f[i]);
+        S* __restrict__ out = fdst + idx;
+        static_for<0, L::Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            Store<S>::st(out + (int64_t)i * plane, f[i]);
+        });
         if constexpr (CHECK) {
-            double du2 = 0.0, u2 = 0.0;
+            R du2 = R(0), u2 = R(0);
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
-                const double u = (double)ur[d];
-                const double up = (double)usnap[(int64_t)d * plane + idx];
-                acc[kStatUx + d] = u;
-                du2 += (u - up) * (u - up);
-                u2 += u * u;
+                const R up = usnap[(int64_t)d * plane + idx];
+                acc[kStatUx + d] = ur[d];
+                du2 += (ur[d] - up) * (ur[d] - up);
+                u2 += ur[d] * ur[d];
                 usnap[(int64_t)d * plane + idx] = ur[d];
             }
             acc[kStatDu2] = du2;
             acc[kStatU2] = u2;
-            acc[kStatDrho] = (double)drho;
-            acc[kStatNonFinite] = isfinite((double)drho) ? 0.0 : 1.0;
+            acc[kStatDrho] = drho;
+            acc[kStatNonFinite] = isfinite(drho) ? R(0) : R(1);
         }
     }
     if constexpr (CHECK) block_sum_store(acc, partials + (int64_t)blockIdx.x * kNumStats);
