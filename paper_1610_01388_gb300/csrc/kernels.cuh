@@ -120,16 +120,31 @@ template <class R> __device__ __forceinline__ const Coef<R>& coef(const KArgs& a
 template <> __device__ __forceinline__ const Coef<float>& coef<float>(const KArgs& a) { return a.cf; }
 template <> __device__ __forceinline__ const Coef<double>& coef<double>(const KArgs& a) { return a.cd; }
 
+// Base pointer of every population plane, passed by value in the kernel
+// parameters: an address is then one multiply-add of the 32-bit cell index.
+template <class S> struct SrcPlanes {
+    const S* p[27];
+};
+template <class S> struct DstPlanes {
+    S* p[27];
+};
+
+// cell index -> (x, y, z)
+__device__ __forceinline__ void cell_xyz(const KParams& kp, int idx, int& x, int& y, int& z) {
+    const uint32_t t = kp.div_nx.div((uint32_t)idx);
+    x = idx - (int)t * kp.nx;
+    z = (int)kp.div_ny.div(t);
+    y = (int)t - z * kp.ny;
+}
+
 // ---------------------------------------------------------------------------
 // streaming (pull) with halfway bounce-back
 template <class L, class S>
-__device__ __forceinline__ void gather(const KParams& kp, const S* __restrict__ f, uint32_t lk,
+__device__ __forceinline__ void gather(const KParams& kp, const SrcPlanes<S>& P, uint32_t lk,
                                        int idx, typename Store<S>::R (&v)[L::Q]) {
     const int nx = kp.nx, ny = kp.ny, nz = kp.nz;
-    const int x = idx % nx;
-    const int t = idx / nx;
-    const int y = t % ny;
-    const int z = t / ny;
+    int x, y, z;
+    cell_xyz(kp, idx, x, y, z);
     // offsets from idx to the source cell x - c for c = +1 (m) and c = -1 (p)
     const int sy = nx, sz = nx * ny;
     const int dxm = (x == 0) ? nx - 1 : -1;
@@ -138,8 +153,6 @@ __device__ __forceinline__ void gather(const KParams& kp, const S* __restrict__ 
     const int dyp = (y == ny - 1) ? -(ny - 1) * sy : sy;
     const int dzm = (z == 0) ? (nz - 1) * sz : -sz;
     const int dzp = (z == nz - 1) ? -(nz - 1) * sz : sz;
-    const int64_t plane = kp.plane;
-    const S* __restrict__ base = f + idx;
     auto offset = [&](auto I) {
         constexpr int i = decltype(I)::value;
         constexpr int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
@@ -156,13 +169,12 @@ __device__ __forceinline__ void gather(const KParams& kp, const S* __restrict__ 
         // no solid neighbour: plain pull, no per-population selects
         static_for<0, L::Q>([&](auto I) {
             constexpr int i = decltype(I)::value;
-            v[i] = Store<S>::ld(base + ((int64_t)i * plane + offset(I)));
+            v[i] = Store<S>::ld(P.p[i] + (idx + offset(I)));
         });
     } else {
         static_for<0, L::Q>([&](auto I) {
             constexpr int i = decltype(I)::value;
-            const S* p = ((lk >> i) & 1u) ? (base + (int64_t)L::opp(i) * plane)
-                                          : (base + ((int64_t)i * plane + offset(I)));
+            const S* p = ((lk >> i) & 1u) ? (P.p[L::opp(i)] + idx) : (P.p[i] + (idx + offset(I)));
             v[i] = Store<S>::ld(p);
         });
     }
@@ -342,7 +354,9 @@ __device__ __forceinline__ void collide_pr(const Coef<R>& c, uint32_t flags, R (
     }
     const R tn = R(0.5) + R(3) * nu;
     const R wp = R(1) / tn;
-    const R wm = R(1) / (R(0.5) + c.magic / (tn - R(0.5)));
+    // 1 / tau_odd with tau_odd = 1/2 + Lambda / (tau - 1/2), as one division
+    const R tm = tn - R(0.5);
+    const R wm = tm / (R(0.5) * tm + c.magic);
     tau = tn;
     const R gx = c.g[0], gy = c.g[1], gz = (L::D == 3) ? c.g[2] : R(0);
     const R Fx = rho * gx, Fy = rho * gy, Fz = rho * gz;
@@ -415,9 +429,22 @@ __device__ __forceinline__ void block_sum_store(V (&v)[kNumStats], double* __res
 
 // ---------------------------------------------------------------------------
 // the fused step
+//
+// Minimum resident blocks per SM requested from the register allocator (0 =
+// let it choose).  Tuning knobs, set at build time.
+#ifndef BLBM_PR_MINB
+#define BLBM_PR_MINB 0
+#endif
+#ifndef BLBM_IR_MINB
+#define BLBM_IR_MINB 0
+#endif
+template <int MODEL> constexpr int step_min_blocks() {
+    return MODEL == LBM_MODEL_PR ? BLBM_PR_MINB : BLBM_IR_MINB;
+}
+
 template <class L, int MODEL, class S, bool CHECK>
-__global__ void __launch_bounds__(kBlock)
-k_step(const KArgs a, const S* __restrict__ fsrc, S* __restrict__ fdst,
+__global__ void __launch_bounds__(kBlock, step_min_blocks<MODEL>())
+k_step(const KArgs a, const SrcPlanes<S> src, const DstPlanes<S> dst,
        const uint32_t* __restrict__ links, typename Store<S>::R* __restrict__ tau,
        typename Store<S>::R* __restrict__ usnap, double* __restrict__ partials) {
     using R = typename Store<S>::R;
@@ -436,7 +463,7 @@ k_step(const KArgs a, const S* __restrict__ fsrc, S* __restrict__ fdst,
     }
     if (active) {
         R f[L::Q];
-        gather<L, S>(kp, fsrc, lk, idx, f);
+        gather<L, S>(kp, src, lk, idx, f);
         R drho, ur[3];
         if constexpr (MODEL == LBM_MODEL_PR) {
             R t = tau[idx];
@@ -445,12 +472,11 @@ k_step(const KArgs a, const S* __restrict__ fsrc, S* __restrict__ fdst,
         } else {
             collide_ir<L, R>(coef<R>(a), kp.flags, f, drho, ur);
         }
-        const int64_t plane = kp.plane;
-        S* __restrict__ out = fdst + idx;
         static_for<0, L::Q>([&](auto I) {
             constexpr int i = decltype(I)::value;
-            Store<S>::st(out + (int64_t)i * plane, f[i]);
+            Store<S>::st(dst.p[i] + idx, f[i]);
         });
+        const int64_t plane = kp.plane;
         if constexpr (CHECK) {
             R du2 = R(0), u2 = R(0);
 #pragma unroll
@@ -473,7 +499,7 @@ k_step(const KArgs a, const S* __restrict__ fsrc, S* __restrict__ fdst,
 // macroscopic fields of the streamed populations
 template <class L, class S>
 __global__ void __launch_bounds__(kBlock)
-k_fields(const KArgs a, const S* __restrict__ f, const uint32_t* __restrict__ links,
+k_fields(const KArgs a, const SrcPlanes<S> f, const uint32_t* __restrict__ links,
          double* __restrict__ rho, double* __restrict__ ux, double* __restrict__ uy,
          double* __restrict__ uz) {
     using R = typename Store<S>::R;
@@ -503,7 +529,7 @@ k_fields(const KArgs a, const S* __restrict__ f, const uint32_t* __restrict__ li
 // grid-stride reductions: flow sums of u_real (gathered) or state totals
 template <class L, class S, int MODE>
 __global__ void __launch_bounds__(kBlock)
-k_reduce(const KArgs a, const S* __restrict__ f, const uint32_t* __restrict__ links,
+k_reduce(const KArgs a, const SrcPlanes<S> f, const uint32_t* __restrict__ links,
          double* __restrict__ partials) {
     using R = typename Store<S>::R;
     const KParams& kp = a.kp;
@@ -519,7 +545,7 @@ k_reduce(const KArgs a, const S* __restrict__ f, const uint32_t* __restrict__ li
             gather<L, S>(kp, f, lk, idx, v);
         } else {
 #pragma unroll
-            for (int i = 0; i < L::Q; ++i) v[i] = Store<S>::ld(f + (int64_t)i * kp.plane + idx);
+            for (int i = 0; i < L::Q; ++i) v[i] = Store<S>::ld(f.p[i] + idx);
         }
         const Mom<R> m = moments<L, R>(v);
         if constexpr (MODE == kReduceFlow) {
@@ -551,7 +577,8 @@ k_links(const KParams kp, const uint8_t* __restrict__ mask, uint32_t* __restrict
         return;
     }
     const int nx = kp.nx, ny = kp.ny, nz = kp.nz;
-    const int x = idx % nx, t = idx / nx, y = t % ny, z = t / ny;
+    int x, y, z;
+    cell_xyz(kp, idx, x, y, z);
     uint32_t bits = 0;
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
@@ -608,17 +635,30 @@ inline KArgs make_args(const KParams& kp) {
     return a;
 }
 
+template <class L, class S> inline SrcPlanes<S> src_planes(const void* f, int64_t plane) {
+    SrcPlanes<S> P{};
+    for (int i = 0; i < L::Q; ++i) P.p[i] = (const S*)f + (int64_t)i * plane;
+    return P;
+}
+template <class L, class S> inline DstPlanes<S> dst_planes(void* f, int64_t plane) {
+    DstPlanes<S> P{};
+    for (int i = 0; i < L::Q; ++i) P.p[i] = (S*)f + (int64_t)i * plane;
+    return P;
+}
+
 template <class L, int MODEL, class S>
 cudaError_t launch_step_t(bool check, const KParams& kp, const StepArgs& s, cudaStream_t st) {
     using R = typename Store<S>::R;
     const KArgs a = make_args(kp);
     const int grid = step_grid(kp.ncells);
+    const SrcPlanes<S> src = src_planes<L, S>(s.fsrc, kp.plane);
+    const DstPlanes<S> dst = dst_planes<L, S>(s.fdst, kp.plane);
     if (check)
         k_step<L, MODEL, S, true><<<grid, kBlock, 0, st>>>(
-            a, (const S*)s.fsrc, (S*)s.fdst, s.links, (R*)s.tau, (R*)s.usnap, s.partials);
+            a, src, dst, s.links, (R*)s.tau, (R*)s.usnap, s.partials);
     else
         k_step<L, MODEL, S, false><<<grid, kBlock, 0, st>>>(
-            a, (const S*)s.fsrc, (S*)s.fdst, s.links, (R*)s.tau, (R*)s.usnap, s.partials);
+            a, src, dst, s.links, (R*)s.tau, (R*)s.usnap, s.partials);
     return cudaGetLastError();
 }
 
@@ -653,10 +693,10 @@ cudaError_t launch_fields_lat(int storage, const KParams& kp, const void* f, con
     const int grid = step_grid(kp.ncells);
     switch (storage) {
     case LBM_F32:
-        k_fields<L, float><<<grid, kBlock, 0, st>>>(a, (const float*)f, links, rho, ux, uy, uz);
+        k_fields<L, float><<<grid, kBlock, 0, st>>>(a, src_planes<L, float>(f, kp.plane), links, rho, ux, uy, uz);
         break;
     case LBM_F64:
-        k_fields<L, double><<<grid, kBlock, 0, st>>>(a, (const double*)f, links, rho, ux, uy, uz);
+        k_fields<L, double><<<grid, kBlock, 0, st>>>(a, src_planes<L, double>(f, kp.plane), links, rho, ux, uy, uz);
         break;
     default: return cudaErrorNotSupported;
     }
@@ -666,10 +706,11 @@ cudaError_t launch_fields_lat(int storage, const KParams& kp, const void* f, con
 template <class L, class S>
 cudaError_t launch_reduce_s(int mode, const KArgs& a, const void* f, const uint32_t* links,
                             double* partials, int nblocks, cudaStream_t st) {
+    const SrcPlanes<S> P = src_planes<L, S>(f, a.kp.plane);
     if (mode == kReduceFlow)
-        k_reduce<L, S, kReduceFlow><<<nblocks, kBlock, 0, st>>>(a, (const S*)f, links, partials);
+        k_reduce<L, S, kReduceFlow><<<nblocks, kBlock, 0, st>>>(a, P, links, partials);
     else
-        k_reduce<L, S, kReduceTotals><<<nblocks, kBlock, 0, st>>>(a, (const S*)f, links, partials);
+        k_reduce<L, S, kReduceTotals><<<nblocks, kBlock, 0, st>>>(a, P, links, partials);
     return cudaGetLastError();
 }
 

@@ -424,6 +424,8 @@ static lbm_status create_impl(lbm_solver** out, lbm_lattice lat, int nx, int ny,
     for (int d = 0; d < 3; ++d) kp.g[d] = p->g[d];
     kp.flags = p->flags;
     kp.half_scale = 1.0;
+    kp.div_nx = FastDiv::make((uint32_t)nx);
+    kp.div_ny = FastDiv::make((uint32_t)ny);
 
     cudaError_t e = cudaGetDevice(&s->device);
     if (e != cudaSuccess) {

@@ -7,6 +7,8 @@
 
 #include <cuda_runtime.h>
 
+#include "fastdiv.h"
+
 namespace blbm {
 
 constexpr int kBlock = 256;          // threads per block of the cell kernels
@@ -23,6 +25,7 @@ struct KParams {
     double g[3];
     uint32_t flags;
     double half_scale;    // reduced-precision storage: offset scale (unused for F32/F64)
+    FastDiv div_nx, div_ny;   // idx -> (x, y, z) without integer division
 };
 
 // Reduction slots.  Check step: flow sums of u_real (x,y,z), sum |u-u_prev|^2,
