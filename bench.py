@@ -38,6 +38,10 @@ if ROOT not in sys.path:
 METRIC = "D3Q27 Bingham MLUPS and % HBM roofline; served solves/s, p50/p99 latency"
 NX, NY, NZ = 256, 128, 128
 LATTICE = "D3Q27"
+STORAGE = "F32"
+STORAGE_CTYPE = {"F32": "float", "F64": "double", "F16": "__half", "BF16": "__nv_bfloat16"}
+STORAGE_DTYPE = {"F32": "f32", "F64": "f64", "F16": "f16 storage / f32 arithmetic",
+                 "BF16": "bf16 storage / f32 arithmetic"}
 NU_P = 0.1
 BN = 2.0
 M_PR = 1e6
@@ -54,10 +58,12 @@ def workload_params():
 def workload_config(extra=None):
     cfg = {"workload": f"square duct {LATTICE} {NX}x{NY}x{NZ} ({NY - 1}x{NZ - 1} fluid "
                        "cross-section), "
-                       f"PR (m={M_PR:g}) + IR per step, Bn={BN:g}, nu_p={NU_P}, FP32 populations, "
+                       f"PR (m={M_PR:g}) + IR per step, Bn={BN:g}, nu_p={NU_P}, {STORAGE} populations, "
                        f"check step every {CHECK_EVERY}",
            "lattice": LATTICE, "nx": NX, "ny": NY, "nz": NZ, "models": ["PR", "IR"],
-           "storage": "F32", "l2": "inputs larger than L2 (2 x 905 MB populations per model)"}
+           "storage": STORAGE,
+           "l2": "inputs larger than L2 (populations per model: "
+                 f"{2 * (19 if LATTICE == 'D3Q19' else 27) * NX * NY * NZ * {'F64': 8, 'F32': 4}.get(STORAGE, 2) / 1e6:.0f} MB)"}
     if extra:
         cfg.update(extra)
     return cfg
@@ -189,7 +195,7 @@ def run_ours(args):
 
     solvers = {}
     for model in ("IR", "PR"):
-        solvers[model] = lbm.Solver(LATTICE, mask, model=model, storage="F32", mu_p=NU_P,
+        solvers[model] = lbm.Solver(LATTICE, mask, model=model, storage=STORAGE, mu_p=NU_P,
                                     sigma_y=sy, m=M_PR, g=(g, 0.0, 0.0),
                                     check_every=CHECK_EVERY, use_torch=True)
     stream = torch.cuda.current_stream(dev)
@@ -237,7 +243,8 @@ def run_ours(args):
                       "achieved_gbs": gbs, "frac": gbs / peak,
                       "mlups": nfluid / t_launch / 1e6}
     dom = "PR" if ms_pr >= ms_ir else "IR"
-    roof = {"bound": "hbm", "kernel": f"k_step<{LATTICE},{dom},float> (dominant by time)",
+    roof = {"bound": "hbm",
+            "kernel": f"k_step<{LATTICE},{dom},{STORAGE_CTYPE[STORAGE]}> (dominant by time)",
             "achieved": round(per[dom]["achieved_gbs"], 1), "peak": peak,
             "peak_kind": f"{peak_kind} (copy bandwidth)", "unit": "GB/s",
             "frac": round(per[dom]["frac"], 4),
@@ -257,7 +264,7 @@ def run_ours(args):
         line = {"metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": ws,
                 "steps": K, "warmup": args.warmup, "ms_per_step": round(max_s * 1e3 / K, 5),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f32", "data": "synthetic",
+                "dtype": STORAGE_DTYPE[STORAGE], "data": "synthetic",
                 "config": workload_config({"per_rank": "independent duct pair per GPU",
                                            "fluid_cells": nfluid}),
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
@@ -281,7 +288,7 @@ def run_e2e(args, mask, nfluid, g, sy, dev):
     barrier()
     t0 = time.perf_counter()
     for model in ("IR", "PR"):
-        p = lbm.lbm_params_default(model=model, storage="F32", mu_p=NU_P, sigma_y=sy, m=M_PR,
+        p = lbm.lbm_params_default(model=model, storage=STORAGE, mu_p=NU_P, sigma_y=sy, m=M_PR,
                                    g=(g, 0.0, 0.0), check_every=CHECK_EVERY)
         h = lbm.lbm_create(LATTICE, mask, p)
         lbm.lbm_step(h, K)
@@ -370,7 +377,7 @@ def run_reference(args):
 
 
 def main(argv=None):
-    global NY, NZ
+    global NX, NY, NZ, LATTICE, STORAGE
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2000)
@@ -381,10 +388,14 @@ def main(argv=None):
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu dram bytes per launch of the dominant kernel, if captured")
+    ap.add_argument("--nx", type=int, default=NX, help="duct length (other workloads)")
     ap.add_argument("--ny", type=int, default=NY, help="duct cross-section (profiling runs)")
+    ap.add_argument("--lattice", default=LATTICE, choices=["D3Q15", "D3Q19", "D3Q27"])
+    ap.add_argument("--storage", default=STORAGE, choices=["F32", "F64", "F16", "BF16"])
     ap.add_argument("--nz", type=int, default=NZ)
     args = ap.parse_args(argv)
-    NY, NZ = args.ny, args.nz
+    NX, NY, NZ = args.nx, args.ny, args.nz
+    LATTICE, STORAGE = args.lattice, args.storage
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":

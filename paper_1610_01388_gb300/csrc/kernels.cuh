@@ -29,6 +29,8 @@
 #include <type_traits>
 #include <utility>
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "../../include/bingham_lbm.h"
@@ -87,17 +89,112 @@ __device__ __forceinline__ R cdot6(R x, R y, R z, R p, R q, R r) {
 }
 
 // ---------------------------------------------------------------------------
-// storage
+// Random bits for stochastic rounding.  Per cell and launch one hash of
+// (cell index, launch counter) with the PCG-based hash of Jarzynski & Olano,
+// "Hash Functions for GPU Rendering" (JCGT 9(3), 2020), then xorshift32
+// steps (Marsaglia, "Xorshift RNGs", JSS 8(14), 2003) for further words.
+__device__ __forceinline__ uint32_t pcg_hash(uint32_t v) {
+    const uint32_t state = v * 747796405u + 2891336453u;
+    const uint32_t word = ((state >> ((state >> 28u) + 4u)) ^ state) * 277803737u;
+    return (word >> 22u) ^ word;
+}
+__device__ __forceinline__ uint32_t xorshift32(uint32_t x) {
+    x ^= x << 13;
+    x ^= x >> 17;
+    x ^= x << 5;
+    return x;
+}
+// Hardware stochastic rounding of two FP32 values to a packed 16-bit pair
+// (PTX cvt.rs, sm_100a and later): the high half holds `hi`, the low half
+// `lo`; rbits supplies the random bits.
+__device__ __forceinline__ uint32_t cvt_rs_f16x2(float hi, float lo, uint32_t rbits) {
+    uint32_t d;
+    asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(rbits));
+    return d;
+}
+__device__ __forceinline__ uint32_t cvt_rs_bf16x2(float hi, float lo, uint32_t rbits) {
+    uint32_t d;
+    asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(rbits));
+    return d;
+}
+__device__ __forceinline__ void st_u16(void* p, uint32_t v) { *reinterpret_cast<uint16_t*>(p) = (uint16_t)v; }
+
+// ---------------------------------------------------------------------------
+// storage.  R is the arithmetic type.  ld / st move the offset f_i - w_i of
+// population i between memory and registers; enc / dec convert full FP64
+// populations at the ABI (set/get populations).
+//
+// The 16-bit forms store the offset normalised by its lattice weight,
+// (f_i - w_i) / w_i, which is O(Ma) in every direction; FP16 also scales it
+// by 2^14 (exact) so offsets down to ~4e-9 stay out of FP16's subnormal range
+// while |(f_i - w_i)/w_i| up to 4 stays below its largest finite value.
 template <class S> struct Store;
 template <> struct Store<float> {
     using R = float;
-    static __device__ __forceinline__ R ld(const float* p) { return __ldg(p); }
-    static __device__ __forceinline__ void st(float* p, R v) { *p = v; }
+    template <class L, int i> static __device__ __forceinline__ R ld(const float* p) { return __ldg(p); }
+    static constexpr bool kStochastic = false;
+    template <class L, int i> static __device__ __forceinline__ void st(float* p, R v, uint32_t) { *p = v; }
+    template <class L, int i>
+    static __device__ __forceinline__ void st2(float* pi, float* po, R vi, R vo, uint32_t) { *pi = vi; *po = vo; }
+    static __device__ __forceinline__ float enc(double off, double) { return (float)off; }
+    static __device__ __forceinline__ double dec(float v, double) { return (double)v; }
 };
 template <> struct Store<double> {
     using R = double;
-    static __device__ __forceinline__ R ld(const double* p) { return __ldg(p); }
-    static __device__ __forceinline__ void st(double* p, R v) { *p = v; }
+    template <class L, int i> static __device__ __forceinline__ R ld(const double* p) { return __ldg(p); }
+    static constexpr bool kStochastic = false;
+    template <class L, int i> static __device__ __forceinline__ void st(double* p, R v, uint32_t) { *p = v; }
+    template <class L, int i>
+    static __device__ __forceinline__ void st2(double* pi, double* po, R vi, R vo, uint32_t) { *pi = vi; *po = vo; }
+    static __device__ __forceinline__ double enc(double off, double) { return off; }
+    static __device__ __forceinline__ double dec(double v, double) { return v; }
+};
+template <> struct Store<__half> {
+    using R = float;
+    static constexpr double kScale = 16384.0;   // 2^14
+    template <class L, int i> static __device__ __forceinline__ R ld(const __half* p) {
+        constexpr float k = float(L::w(i) / kScale);
+        return __half2float(__ldg(p)) * k;
+    }
+    static constexpr bool kStochastic = true;
+    // stochastic rounding (unbiased: a value moves by less than half an ulp per
+    // step in slowly relaxing flows, and round-to-nearest would freeze it)
+    template <class L, int i> static __device__ __forceinline__ void st(__half* p, R v, uint32_t rnd) {
+        constexpr float k = float(kScale / L::w(i));
+        st_u16(p, cvt_rs_f16x2(v * k, 0.0f, rnd) >> 16);
+    }
+    // populations i and its opposite (same weight) in one conversion
+    template <class L, int i>
+    static __device__ __forceinline__ void st2(__half* pi, __half* po, R vi, R vo, uint32_t rnd) {
+        constexpr float k = float(kScale / L::w(i));
+        const uint32_t d = cvt_rs_f16x2(vi * k, vo * k, rnd);
+        st_u16(pi, d >> 16);
+        st_u16(po, d);
+    }
+    static __device__ __forceinline__ __half enc(double off, double w) { return __double2half(off / w * kScale); }
+    static __device__ __forceinline__ double dec(__half v, double w) { return (double)__half2float(v) * (w / kScale); }
+};
+template <> struct Store<__nv_bfloat16> {
+    using R = float;
+    template <class L, int i> static __device__ __forceinline__ R ld(const __nv_bfloat16* p) {
+        constexpr float k = float(L::w(i));
+        return __bfloat162float(__ldg(p)) * k;
+    }
+    static constexpr bool kStochastic = true;
+    template <class L, int i> static __device__ __forceinline__ void st(__nv_bfloat16* p, R v, uint32_t rnd) {
+        constexpr float k = float(1.0 / L::w(i));
+        st_u16(p, cvt_rs_bf16x2(v * k, 0.0f, rnd) >> 16);
+    }
+    template <class L, int i>
+    static __device__ __forceinline__ void st2(__nv_bfloat16* pi, __nv_bfloat16* po, R vi, R vo,
+                                               uint32_t rnd) {
+        constexpr float k = float(1.0 / L::w(i));
+        const uint32_t d = cvt_rs_bf16x2(vi * k, vo * k, rnd);
+        st_u16(pi, d >> 16);
+        st_u16(po, d);
+    }
+    static __device__ __forceinline__ __nv_bfloat16 enc(double off, double w) { return __double2bfloat16(off / w); }
+    static __device__ __forceinline__ double dec(__nv_bfloat16 v, double w) { return (double)__bfloat162float(v) * w; }
 };
 
 // Rheology constants in the arithmetic type, derived on the host in FP64.
@@ -169,13 +266,13 @@ __device__ __forceinline__ void gather(const KParams& kp, const SrcPlanes<S>& P,
         // no solid neighbour: plain pull, no per-population selects
         static_for<0, L::Q>([&](auto I) {
             constexpr int i = decltype(I)::value;
-            v[i] = Store<S>::ld(P.p[i] + (idx + offset(I)));
+            v[i] = Store<S>::template ld<L, i>(P.p[i] + (idx + offset(I)));
         });
     } else {
         static_for<0, L::Q>([&](auto I) {
             constexpr int i = decltype(I)::value;
             const S* p = ((lk >> i) & 1u) ? (P.p[L::opp(i)] + idx) : (P.p[i] + (idx + offset(I)));
-            v[i] = Store<S>::ld(p);
+            v[i] = Store<S>::template ld<L, i>(p);   // opposite planes share w_i
         });
     }
 }
@@ -446,11 +543,19 @@ template <class L, int MODEL, class S, bool CHECK>
 __global__ void __launch_bounds__(kBlock, step_min_blocks<MODEL>())
 k_step(const KArgs a, const SrcPlanes<S> src, const DstPlanes<S> dst,
        const uint32_t* __restrict__ links, typename Store<S>::R* __restrict__ tau,
-       typename Store<S>::R* __restrict__ usnap, double* __restrict__ partials) {
+       typename Store<S>::R* __restrict__ usnap, double* __restrict__ partials,
+       uint32_t* __restrict__ rng_ctr, int parity) {
     using R = typename Store<S>::R;
     const KParams& kp = a.kp;
     const int idx = blockIdx.x * kBlock + threadIdx.x;
     const bool inside = idx < kp.ncells;
+    uint32_t rnd = 0u;
+    if constexpr (Store<S>::kStochastic) {
+        // this launch reads counter[parity] and leaves counter + 1 for the next
+        const uint32_t seed = __ldg(rng_ctr + parity);
+        if (blockIdx.x == 0 && threadIdx.x == 0) rng_ctr[parity ^ 1] = seed + 1u;
+        rnd = pcg_hash((uint32_t)idx ^ (seed * 0x9e3779b9u));
+    }
     const uint32_t lk = inside ? __ldg(links + idx) : kSolidBit;
     const bool active = !(lk & kSolidBit);
     if constexpr (!CHECK) {
@@ -472,9 +577,12 @@ k_step(const KArgs a, const SrcPlanes<S> src, const DstPlanes<S> dst,
         } else {
             collide_ir<L, R>(coef<R>(a), kp.flags, f, drho, ur);
         }
-        static_for<0, L::Q>([&](auto I) {
-            constexpr int i = decltype(I)::value;
-            Store<S>::st(dst.p[i] + idx, f[i]);
+        // rest population, then opposite pairs (i, i + 1), one random word each
+        Store<S>::template st<L, 0>(dst.p[0] + idx, f[0], rnd);
+        static_for<0, (L::Q - 1) / 2>([&](auto P) {
+            constexpr int i = 2 * decltype(P)::value + 1;
+            if constexpr (Store<S>::kStochastic) rnd = xorshift32(rnd);
+            Store<S>::template st2<L, i>(dst.p[i] + idx, dst.p[i + 1] + idx, f[i], f[i + 1], rnd);
         });
         const int64_t plane = kp.plane;
         if constexpr (CHECK) {
@@ -544,8 +652,10 @@ k_reduce(const KArgs a, const SrcPlanes<S> f, const uint32_t* __restrict__ links
         if constexpr (MODE == kReduceFlow) {
             gather<L, S>(kp, f, lk, idx, v);
         } else {
-#pragma unroll
-            for (int i = 0; i < L::Q; ++i) v[i] = Store<S>::ld(f.p[i] + idx);
+            static_for<0, L::Q>([&](auto I) {
+                constexpr int i = decltype(I)::value;
+                v[i] = Store<S>::template ld<L, i>(f.p[i] + idx);
+            });
         }
         const Mom<R> m = moments<L, R>(v);
         if constexpr (MODE == kReduceFlow) {
@@ -602,9 +712,9 @@ k_convert(const KParams kp, int q, bool to_device, S* __restrict__ f, double* __
         if (i == q) w = L::w(i);
     S* p = f + (int64_t)q * kp.plane + idx;
     if (to_device)
-        *p = (S)(buf[idx] - w);
+        *p = Store<S>::enc(buf[idx] - w, w);
     else
-        buf[idx] = (double)*p + w;
+        buf[idx] = Store<S>::dec(*p, w) + w;
 }
 
 // ---------------------------------------------------------------------------
@@ -655,10 +765,10 @@ cudaError_t launch_step_t(bool check, const KParams& kp, const StepArgs& s, cuda
     const DstPlanes<S> dst = dst_planes<L, S>(s.fdst, kp.plane);
     if (check)
         k_step<L, MODEL, S, true><<<grid, kBlock, 0, st>>>(
-            a, src, dst, s.links, (R*)s.tau, (R*)s.usnap, s.partials);
+            a, src, dst, s.links, (R*)s.tau, (R*)s.usnap, s.partials, s.rng_ctr, s.parity);
     else
         k_step<L, MODEL, S, false><<<grid, kBlock, 0, st>>>(
-            a, src, dst, s.links, (R*)s.tau, (R*)s.usnap, s.partials);
+            a, src, dst, s.links, (R*)s.tau, (R*)s.usnap, s.partials, s.rng_ctr, s.parity);
     return cudaGetLastError();
 }
 
@@ -675,6 +785,8 @@ cudaError_t launch_step_lat(int model, int storage, bool check, const KParams& k
     switch (storage) {
     case LBM_F32: return launch_step_model<L, float>(model, check, kp, s, st);
     case LBM_F64: return launch_step_model<L, double>(model, check, kp, s, st);
+    case LBM_F16_OFS: return launch_step_model<L, __half>(model, check, kp, s, st);
+    case LBM_BF16_OFS: return launch_step_model<L, __nv_bfloat16>(model, check, kp, s, st);
     default: return cudaErrorNotSupported;
     }
 }
@@ -697,6 +809,12 @@ cudaError_t launch_fields_lat(int storage, const KParams& kp, const void* f, con
         break;
     case LBM_F64:
         k_fields<L, double><<<grid, kBlock, 0, st>>>(a, src_planes<L, double>(f, kp.plane), links, rho, ux, uy, uz);
+        break;
+    case LBM_F16_OFS:
+        k_fields<L, __half><<<grid, kBlock, 0, st>>>(a, src_planes<L, __half>(f, kp.plane), links, rho, ux, uy, uz);
+        break;
+    case LBM_BF16_OFS:
+        k_fields<L, __nv_bfloat16><<<grid, kBlock, 0, st>>>(a, src_planes<L, __nv_bfloat16>(f, kp.plane), links, rho, ux, uy, uz);
         break;
     default: return cudaErrorNotSupported;
     }
@@ -722,6 +840,8 @@ cudaError_t launch_reduce_lat(int storage, int mode, const KParams& kp, const vo
     switch (storage) {
     case LBM_F32: return launch_reduce_s<L, float>(mode, a, f, links, partials, nblocks, st);
     case LBM_F64: return launch_reduce_s<L, double>(mode, a, f, links, partials, nblocks, st);
+    case LBM_F16_OFS: return launch_reduce_s<L, __half>(mode, a, f, links, partials, nblocks, st);
+    case LBM_BF16_OFS: return launch_reduce_s<L, __nv_bfloat16>(mode, a, f, links, partials, nblocks, st);
     default: return cudaErrorNotSupported;
     }
 }
@@ -733,6 +853,8 @@ cudaError_t launch_convert_lat(int storage, bool to_device, const KParams& kp, i
     switch (storage) {
     case LBM_F32: k_convert<L, float><<<grid, kBlock, 0, st>>>(kp, q, to_device, (float*)f, buf); break;
     case LBM_F64: k_convert<L, double><<<grid, kBlock, 0, st>>>(kp, q, to_device, (double*)f, buf); break;
+    case LBM_F16_OFS: k_convert<L, __half><<<grid, kBlock, 0, st>>>(kp, q, to_device, (__half*)f, buf); break;
+    case LBM_BF16_OFS: k_convert<L, __nv_bfloat16><<<grid, kBlock, 0, st>>>(kp, q, to_device, (__nv_bfloat16*)f, buf); break;
     default: return cudaErrorNotSupported;
     }
     return cudaGetLastError();

@@ -8,7 +8,8 @@
 //   tau       PR relaxation time per cell, updated in place
 //   usnap     check-step velocity snapshot [3][plane]
 //   partials  per-block FP64 reduction partials
-//   stats     finalised reduction results
+//   stats     finalised reduction results, then two u32 launch counters
+//             (stochastic rounding of the 16-bit storage forms)
 //   mask      the uploaded solid mask (bytes)
 #include <cmath>
 #include <cstdarg>
@@ -60,7 +61,7 @@ size_t storage_bytes(int storage) {
 
 size_t arith_bytes(int storage) { return storage == LBM_F64 ? 8 : 4; }
 
-bool storage_built(int storage) { return storage == LBM_F32 || storage == LBM_F64; }
+bool storage_built(int storage) { return storage_bytes(storage) != 0; }
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
@@ -182,6 +183,8 @@ cudaError_t launch_step(lbm_solver* s, bool check, cudaStream_t st) {
     a.tau = s->tau;
     a.usnap = s->usnap;
     a.partials = s->partials;
+    a.rng_ctr = (uint32_t*)(s->stats + 2 * kNumStats);
+    a.parity = s->cur;
     switch (s->lat) {
     case LBM_D2Q9: return launch_step_D2Q9(s->p.model, s->p.storage, check, s->kp, a, st);
     case LBM_D3Q15: return launch_step_D3Q15(s->p.model, s->p.storage, check, s->kp, a, st);
@@ -481,7 +484,8 @@ static lbm_status create_impl(lbm_solver** out, lbm_lattice lat, int nx, int ny,
         if (s->usnap) {
             if ((e = cudaMemsetAsync(s->usnap, 0, (size_t)3 * s->lay.plane * arith_bytes(p->storage), s->stream)) != cudaSuccess) break;
         }
-        if ((e = cudaMemsetAsync(s->stats, 0, 2 * kNumStats * sizeof(double), s->stream)) != cudaSuccess) break;
+        // stats (2 x kNumStats doubles) and the two rounding counters behind them
+        if ((e = cudaMemsetAsync(s->stats, 0, 256, s->stream)) != cudaSuccess) break;
         e = cudaStreamSynchronize(s->stream);
     } while (0);
     if (rc == LBM_OK && e != cudaSuccess) rc = cuda_fail(nullptr, e, "solver initialisation");

@@ -41,6 +41,8 @@ struct StepArgs {
     void* tau;           // PR relaxation-time field, updated in place (R per cell)
     void* usnap;         // check step: u snapshot [3][plane] (R)
     double* partials;    // check step: [gridDim][kNumStats]
+    uint32_t* rng_ctr;   // 16-bit storage: launch counters for stochastic rounding [2]
+    int parity;          // which of the two counters this launch reads
 };
 
 enum ReduceMode { kReduceFlow = 0, kReduceTotals = 1 };

@@ -1,0 +1,91 @@
+"""Parity at the full workload sizes, in the launch configuration bench.py
+times (FP32, CUDA-graph replay of long step runs), on sampled cells.
+
+The GPU state after n steps is read back (FP32 offsets -> FP64 full f); the
+oracle computes one more step for a sample of cells from exactly that state
+(its per-population FP64 collision); the GPU takes the same step and the two
+are compared cell by cell.  Whole-domain invariants (mass) are checked too.
+"""
+import numpy as np
+import pytest
+
+from paper_1610_01388_gb300 import lbm
+from paper_1610_01388_gb300 import workloads as W
+
+from _pairs import gpu_to_oracle, make_pair, perm_gpu_to_oracle
+
+pytestmark = pytest.mark.gpu
+
+
+def _sample(mask, n, seed):
+    rng = np.random.default_rng(seed)
+    flat = mask.reshape(-1)
+    fluid = np.flatnonzero(flat == 0)
+    pick = rng.choice(fluid, size=min(n, fluid.size), replace=False)
+    # every fluid cell of a few wall-adjacent and wrap rows as well
+    nz, ny, nx = mask.shape
+    extra = []
+    for z, y in ((1, 1), (1, ny - 1), (nz - 1, 1), (nz // 2, ny // 2), (nz - 1, ny - 1)):
+        if 0 <= z < nz and 0 <= y < ny:
+            row = z * ny * nx + y * nx + np.arange(nx)
+            extra.append(row[flat[row] == 0])
+    return np.unique(np.concatenate([pick] + extra)).astype(np.int64)
+
+
+def _sampled_step_parity(lat, mask, model, steps, **kw):
+    s, o = make_pair(lat, mask, model=model, storage="F32", check_every=100, **kw)
+    s.step(steps)                                  # graph replay path
+    m0, _ = s.totals()
+    f_state = gpu_to_oracle(lat, s.get_populations())
+    o.f = np.ascontiguousarray(f_state)
+    if model == "PR":
+        o.tau = np.ascontiguousarray(s.get_tau().reshape(-1))
+    cells = _sample(mask, 4000, seed=steps)
+    want, want_tau = o.step_cells(cells)           # oracle: one step of the sampled cells
+    s.step(1)
+    got_all = gpu_to_oracle(lat, s.get_populations())
+    got = got_all[:, cells].T
+    scale = np.max(np.abs(want - o.w[None, :]))
+    err = np.max(np.abs(got - want)) / scale
+    assert err < 1e-5, (lat, model, err)
+    if model == "PR":
+        got_tau = s.get_tau().reshape(-1)[cells]
+        assert np.max(np.abs(got_tau - want_tau) / want_tau) < 1e-5
+    m1, _ = s.totals()
+    assert abs(m1 - m0) / m0 < 1e-6
+    s.close()
+    return err
+
+
+@pytest.mark.parametrize("lat", ["D3Q27", "D3Q19"])
+@pytest.mark.parametrize("model", ["PR", "IR"])
+def test_fullsize_square_duct(lat, model):
+    """Square duct 256 x 128 x 128 (127 x 127 fluid), Bn = 2, from rest."""
+    prm = W.duct_params(H=127, nu_p=0.1, u_newton=0.02, bn=2.0)
+    mask = W.duct_mask(256, 128, 128)
+    _sampled_step_parity(lat, mask, model, 300, nu_p=0.1, sigma_y=prm["sigma_y"], m=1e6,
+                         g=(prm["g"], 0.0, 0.0))
+
+
+@pytest.mark.parametrize("model", ["PR", "IR"])
+def test_fullsize_porous_d3q19(model):
+    """Porous box 256^3, random non-overlapping spheres r in [6, 10], porosity
+    0.7, seed 1, body-force driven."""
+    mask, info = W.porous_mask(256, porosity=0.7, r_min=6, r_max=10, seed=1)
+    assert info["reached"]
+    _sampled_step_parity("D3Q19", mask, model, 200, nu_p=0.1, sigma_y=2e-6, m=1e6,
+                         g=(2e-6, 0.0, 0.0))
+
+
+def test_fullsize_channel_fp64_20k_steps():
+    """Channel 4 x 64, D2Q9, FP64, 20k steps from rest, both models: the whole
+    field against the oracle at equal step count."""
+    from _pairs import rel_l2_u
+    prm = W.channel_params(H=63, nu_p=0.1, u_newton=0.01, bn=1.0)
+    for model in ("PR", "IR"):
+        s, o = make_pair("D2Q9", W.channel_mask(4, 64), model=model, storage="F64",
+                         sigma_y=prm["sigma_y"], m=1e4, g=(prm["g"], 0, 0))
+        s.step(20000)
+        o.step(20000)
+        assert rel_l2_u(s, o) < 1e-11
+        s.close()
