@@ -218,6 +218,105 @@ lbm_status lbm_flowrate_noalloc(lbm_solver *s, int axis, double *q_device);
 /* Releases the handle and the device memory the library allocated. */
 void lbm_destroy(lbm_solver *s);
 
+/* ------------------------------------------------------------------------
+ * Batched stepping of many resident domains (no counterpart in the paper: a
+ * throughput form for many small, independent solves).
+ *
+ * A batch owns any number of domains, each a full solver (any lattice, model,
+ * storage, extents, rheology).  lbm_batch_step advances ALL of them: one
+ * launch per (lattice, model, storage) combination present covers every
+ * domain of that combination, long runs are replayed as CUDA graphs, and
+ * every check_every-th step also computes each domain's residual and flow
+ * rate.  Each domain's arithmetic is identical to lbm_step's (same device
+ * code), so a domain's result does not depend on the other domains in the
+ * batch (for the 16-bit storage forms up to the stochastic-rounding draw).
+ * Device memory of each domain is taken from the CUDA stream-ordered memory
+ * pool; the batch admits a domain only if the sum of all domains' bytes stays
+ * within device_budget_bytes (LBM_EBUSY otherwise).  All work runs on the
+ * batch's stream.  Domains need Q * cells < 2^31.
+ * ------------------------------------------------------------------------ */
+typedef struct lbm_batch lbm_batch;
+
+typedef struct {
+    int64_t steps;      /* time steps this domain has taken */
+    int64_t checks;     /* check steps it has seen */
+    double residual;    /* last check step; -1 before two check steps */
+    double flow_x;      /* flow rate along x at the last check step */
+    int32_t nonfinite;  /* 1 if the last check step saw a non-finite density */
+    int32_t pad;
+} lbm_domain_status;
+
+lbm_status lbm_batch_create(lbm_batch **out, size_t device_budget_bytes, int32_t check_every,
+                            void *cuda_stream);
+/* Adds a domain at rest (as lbm_create; p->check_every is replaced by the
+ * batch's).  *domain_id receives its handle. */
+lbm_status lbm_batch_add(lbm_batch *b, lbm_lattice lat, int nx, int ny, int nz,
+                         const uint8_t *solid_mask, const lbm_params *p, int64_t *domain_id);
+lbm_status lbm_batch_remove(lbm_batch *b, int64_t domain_id);
+lbm_status lbm_batch_step(lbm_batch *b, int64_t nsteps);
+/* Synchronises and reports the domain's last check step. */
+lbm_status lbm_batch_domain_status(lbm_batch *b, int64_t domain_id, lbm_domain_status *st);
+/* Borrows the domain's solver handle for lbm_fields / lbm_flowrate /
+ * lbm_get_populations / ...; valid until the domain is removed; must not be
+ * destroyed or stepped directly (use lbm_batch_step). */
+lbm_status lbm_batch_solver(lbm_batch *b, int64_t domain_id, lbm_solver **s);
+lbm_status lbm_batch_usage(const lbm_batch *b, size_t *bytes_used, int64_t *domains,
+                           int64_t *fluid_cells);
+void lbm_batch_destroy(lbm_batch *b);
+
+/* ------------------------------------------------------------------------
+ * Serving with continuous batching (no counterpart in the paper).
+ *
+ * Requests (independent solves) are submitted at any time and queued on the
+ * host.  Each lbm_server_advance call admits queued requests while the
+ * device-memory budget allows (in submission order, letting a smaller later
+ * request in when an earlier one does not fit), advances every running
+ * solve together by nsteps (a multiple of check_every) through one batch,
+ * and retires the solves whose residual fell below their tolerance or that
+ * reached their step cap, freeing their memory for the next admissions.
+ * Times are seconds on the server's monotonic clock (lbm_server_now).
+ * ------------------------------------------------------------------------ */
+typedef struct lbm_server lbm_server;
+
+typedef struct {
+    int32_t lattice, nx, ny, nz;
+    const uint8_t *solid_mask;  /* host, nx*ny*nz, copied at submit */
+    lbm_params params;
+    double tolerance;           /* steady state: residual < tolerance */
+    int64_t max_steps;          /* step cap (> 0) */
+    int32_t keep_fields;        /* keep rho and u_real of the final state on the host */
+    int32_t pad;
+} lbm_request;
+
+enum { LBM_REQ_QUEUED = 0, LBM_REQ_RUNNING = 1, LBM_REQ_CONVERGED = 2, LBM_REQ_CAPPED = 3,
+       LBM_REQ_FAILED = 4 };
+
+typedef struct {
+    int32_t state;              /* LBM_REQ_* */
+    int32_t pad;
+    int64_t steps;
+    int64_t fluid_cells;
+    double residual;            /* at completion */
+    double flow_x;              /* flow rate along x at completion (lbm_flowrate) */
+    double t_submit, t_admit, t_done;
+} lbm_result;
+
+lbm_status lbm_server_create(lbm_server **out, size_t device_budget_bytes, int32_t check_every,
+                             void *cuda_stream);
+/* Queues a request; LBM_EINVAL if it is malformed or could never fit the
+ * budget.  *request_id receives its handle. */
+lbm_status lbm_server_submit(lbm_server *s, const lbm_request *req, int64_t *request_id);
+lbm_status lbm_server_advance(lbm_server *s, int64_t nsteps, int32_t *completed);
+lbm_status lbm_server_result(const lbm_server *s, int64_t request_id, lbm_result *res);
+/* rho / u_real (N doubles each, host, any may be NULL) of a completed
+ * request submitted with keep_fields. */
+lbm_status lbm_server_fields(const lbm_server *s, int64_t request_id, double *rho, double *ux,
+                             double *uy, double *uz);
+lbm_status lbm_server_pending(const lbm_server *s, int64_t *queued, int64_t *running,
+                              size_t *bytes_used);
+lbm_status lbm_server_now(const lbm_server *s, double *t);
+void lbm_server_destroy(lbm_server *s);
+
 /* Thread-local message of the last failing call on this thread. */
 const char *lbm_last_error(void);
 const char *lbm_status_string(lbm_status st);

@@ -221,9 +221,24 @@ template <> __device__ __forceinline__ const Coef<double>& coef<double>(const KA
 // parameters: an address is then one multiply-add of the 32-bit cell index.
 template <class S> struct SrcPlanes {
     const S* p[27];
+    template <int i> __device__ __forceinline__ const S* at(int n) const { return p[i] + n; }
 };
 template <class S> struct DstPlanes {
     S* p[27];
+    template <int i> __device__ __forceinline__ S* at(int n) const { return p[i] + n; }
+};
+// Planes of one buffer addressed by a stride (batched launches, where the
+// pointers differ per domain): element i * plane + n, in 32-bit arithmetic
+// (the batch admits only domains with Q * plane < 2^31).
+template <class S> struct SrcStride {
+    const S* base;
+    int plane;
+    template <int i> __device__ __forceinline__ const S* at(int n) const { return base + (i * plane + n); }
+};
+template <class S> struct DstStride {
+    S* base;
+    int plane;
+    template <int i> __device__ __forceinline__ S* at(int n) const { return base + (i * plane + n); }
 };
 
 // cell index -> (x, y, z)
@@ -236,8 +251,8 @@ __device__ __forceinline__ void cell_xyz(const KParams& kp, int idx, int& x, int
 
 // ---------------------------------------------------------------------------
 // streaming (pull) with halfway bounce-back
-template <class L, class S>
-__device__ __forceinline__ void gather(const KParams& kp, const SrcPlanes<S>& P, uint32_t lk,
+template <class L, class S, class Src>
+__device__ __forceinline__ void gather(const KParams& kp, const Src& P, uint32_t lk,
                                        int idx, typename Store<S>::R (&v)[L::Q]) {
     const int nx = kp.nx, ny = kp.ny, nz = kp.nz;
     int x, y, z;
@@ -266,12 +281,13 @@ __device__ __forceinline__ void gather(const KParams& kp, const SrcPlanes<S>& P,
         // no solid neighbour: plain pull, no per-population selects
         static_for<0, L::Q>([&](auto I) {
             constexpr int i = decltype(I)::value;
-            v[i] = Store<S>::template ld<L, i>(P.p[i] + (idx + offset(I)));
+            v[i] = Store<S>::template ld<L, i>(P.template at<i>(idx + offset(I)));
         });
     } else {
         static_for<0, L::Q>([&](auto I) {
             constexpr int i = decltype(I)::value;
-            const S* p = ((lk >> i) & 1u) ? (P.p[L::opp(i)] + idx) : (P.p[i] + (idx + offset(I)));
+            const S* p = ((lk >> i) & 1u) ? P.template at<L::opp(i)>(idx)
+                                          : P.template at<i>(idx + offset(I));
             v[i] = Store<S>::template ld<L, i>(p);   // opposite planes share w_i
         });
     }
@@ -539,6 +555,52 @@ template <int MODEL> constexpr int step_min_blocks() {
     return MODEL == LBM_MODEL_PR ? BLBM_PR_MINB : BLBM_IR_MINB;
 }
 
+// One cell of one time step: pull, collide, store; on check steps the cell's
+// contributions to the flow-rate and residual sums go to acc.  Shared by the
+// single-domain and the batched kernels so both do identical arithmetic.
+template <class L, int MODEL, class S, bool CHECK, class Src, class Dst>
+__device__ __forceinline__ void cell_step(const KParams& kp, const Coef<typename Store<S>::R>& c,
+                                          const Src& src, const Dst& dst, uint32_t lk, int idx,
+                                          typename Store<S>::R* __restrict__ tau,
+                                          typename Store<S>::R* __restrict__ usnap, uint32_t rnd,
+                                          typename Store<S>::R (&acc)[kNumStats]) {
+    using R = typename Store<S>::R;
+    R f[L::Q];
+    gather<L, S>(kp, src, lk, idx, f);
+    R drho, ur[3];
+    if constexpr (MODEL == LBM_MODEL_PR) {
+        R t = tau[idx];
+        collide_pr<L, R>(c, kp.flags, f, t, drho, ur);
+        tau[idx] = t;
+    } else {
+        collide_ir<L, R>(c, kp.flags, f, drho, ur);
+    }
+    // rest population, then opposite pairs (i, i + 1), one random word each
+    Store<S>::template st<L, 0>(dst.template at<0>(idx), f[0], rnd);
+    static_for<0, (L::Q - 1) / 2>([&](auto P) {
+        constexpr int i = 2 * decltype(P)::value + 1;
+        if constexpr (Store<S>::kStochastic) rnd = xorshift32(rnd);
+        Store<S>::template st2<L, i>(dst.template at<i>(idx), dst.template at<i + 1>(idx), f[i],
+                                     f[i + 1], rnd);
+    });
+    if constexpr (CHECK) {
+        const int64_t plane = kp.plane;
+        R du2 = R(0), u2 = R(0);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const R up = usnap[(int64_t)d * plane + idx];
+            acc[kStatUx + d] = ur[d];
+            du2 += (ur[d] - up) * (ur[d] - up);
+            u2 += ur[d] * ur[d];
+            usnap[(int64_t)d * plane + idx] = ur[d];
+        }
+        acc[kStatDu2] = du2;
+        acc[kStatU2] = u2;
+        acc[kStatDrho] = drho;
+        acc[kStatNonFinite] = isfinite(drho) ? R(0) : R(1);
+    }
+}
+
 template <class L, int MODEL, class S, bool CHECK>
 __global__ void __launch_bounds__(kBlock, step_min_blocks<MODEL>())
 k_step(const KArgs a, const SrcPlanes<S> src, const DstPlanes<S> dst,
@@ -566,41 +628,68 @@ k_step(const KArgs a, const SrcPlanes<S> src, const DstPlanes<S> dst,
 #pragma unroll
         for (int k = 0; k < kNumStats; ++k) acc[k] = R(0);
     }
-    if (active) {
-        R f[L::Q];
-        gather<L, S>(kp, src, lk, idx, f);
-        R drho, ur[3];
-        if constexpr (MODEL == LBM_MODEL_PR) {
-            R t = tau[idx];
-            collide_pr<L, R>(coef<R>(a), kp.flags, f, t, drho, ur);
-            tau[idx] = t;
-        } else {
-            collide_ir<L, R>(coef<R>(a), kp.flags, f, drho, ur);
-        }
-        // rest population, then opposite pairs (i, i + 1), one random word each
-        Store<S>::template st<L, 0>(dst.p[0] + idx, f[0], rnd);
-        static_for<0, (L::Q - 1) / 2>([&](auto P) {
-            constexpr int i = 2 * decltype(P)::value + 1;
-            if constexpr (Store<S>::kStochastic) rnd = xorshift32(rnd);
-            Store<S>::template st2<L, i>(dst.p[i] + idx, dst.p[i + 1] + idx, f[i], f[i + 1], rnd);
-        });
-        const int64_t plane = kp.plane;
-        if constexpr (CHECK) {
-            R du2 = R(0), u2 = R(0);
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                const R up = usnap[(int64_t)d * plane + idx];
-                acc[kStatUx + d] = ur[d];
-                du2 += (ur[d] - up) * (ur[d] - up);
-                u2 += ur[d] * ur[d];
-                usnap[(int64_t)d * plane + idx] = ur[d];
-            }
-            acc[kStatDu2] = du2;
-            acc[kStatU2] = u2;
-            acc[kStatDrho] = drho;
-            acc[kStatNonFinite] = isfinite(drho) ? R(0) : R(1);
-        }
+    if (active) cell_step<L, MODEL, S, CHECK>(kp, coef<R>(a), src, dst, lk, idx, tau, usnap, rnd, acc);
+    if constexpr (CHECK) block_sum_store(acc, partials + (int64_t)blockIdx.x * kNumStats);
+}
+
+// ---------------------------------------------------------------------------
+// Batched step: all resident domains of one (lattice, model, storage) in one
+// launch.  Block b works on domain block_dom[b]; each domain's blocks are
+// contiguous from desc.block_begin.  The current buffer of a domain is
+// phase ^ desc.parity0, so a captured graph that alternates the phase stays
+// valid for every domain.
+struct BatchDesc {
+    KParams kp;
+    Coef<float> cf;
+    Coef<double> cd;
+    void* f[2];
+    const uint32_t* links;
+    void* tau;
+    void* usnap;
+    uint32_t* rng;      // two launch counters (16-bit storage)
+    int parity0;
+    int block_begin;
+    int nblocks;
+    int slot;           // row of this domain in the batch's per-domain stats
+};
+
+template <class R> __device__ __forceinline__ const Coef<R>& bcoef(const BatchDesc& d);
+template <> __device__ __forceinline__ const Coef<float>& bcoef<float>(const BatchDesc& d) { return d.cf; }
+template <> __device__ __forceinline__ const Coef<double>& bcoef<double>(const BatchDesc& d) { return d.cd; }
+
+template <class L, int MODEL, class S, bool CHECK>
+__global__ void __launch_bounds__(kBlock)
+k_step_batch(const BatchDesc* __restrict__ descs, const int* __restrict__ block_dom, int phase,
+             double* __restrict__ partials) {
+    using R = typename Store<S>::R;
+    const BatchDesc& D = descs[block_dom[blockIdx.x]];
+    const KParams& kp = D.kp;
+    const int lb = blockIdx.x - D.block_begin;
+    const int idx = lb * kBlock + threadIdx.x;
+    const int cur = phase ^ D.parity0;
+    const SrcStride<S> src{(const S*)D.f[cur], (int)kp.plane};
+    const DstStride<S> dst{(S*)D.f[cur ^ 1], (int)kp.plane};
+    const bool inside = idx < kp.ncells;
+    uint32_t rnd = 0u;
+    if constexpr (Store<S>::kStochastic) {
+        // reads counter[cur], leaves counter + 1 in the other slot for the next launch
+        const uint32_t seed = D.rng[cur];
+        if (lb == 0 && threadIdx.x == 0) D.rng[cur ^ 1] = seed + 1u;
+        rnd = pcg_hash((uint32_t)idx ^ (seed * 0x9e3779b9u));
     }
+    const uint32_t lk = inside ? __ldg(D.links + idx) : kSolidBit;
+    const bool active = !(lk & kSolidBit);
+    if constexpr (!CHECK) {
+        if (!active) return;
+    }
+    R acc[kNumStats];
+    if constexpr (CHECK) {
+#pragma unroll
+        for (int k = 0; k < kNumStats; ++k) acc[k] = R(0);
+    }
+    if (active)
+        cell_step<L, MODEL, S, CHECK>(kp, bcoef<R>(D), src, dst, lk, idx, (R*)D.tau, (R*)D.usnap,
+                                      rnd, acc);
     if constexpr (CHECK) block_sum_store(acc, partials + (int64_t)blockIdx.x * kNumStats);
 }
 
@@ -791,6 +880,37 @@ cudaError_t launch_step_lat(int model, int storage, bool check, const KParams& k
     }
 }
 
+template <class L, int MODEL, class S>
+cudaError_t launch_batch_t(bool check, const BatchDesc* descs, const int* block_dom, int nblocks,
+                           int phase, double* partials, cudaStream_t st) {
+    if (check)
+        k_step_batch<L, MODEL, S, true><<<nblocks, kBlock, 0, st>>>(descs, block_dom, phase, partials);
+    else
+        k_step_batch<L, MODEL, S, false><<<nblocks, kBlock, 0, st>>>(descs, block_dom, phase, partials);
+    return cudaGetLastError();
+}
+
+template <class L, class S>
+cudaError_t launch_batch_model(int model, bool check, const BatchDesc* descs, const int* block_dom,
+                               int nblocks, int phase, double* partials, cudaStream_t st) {
+    if (model == LBM_MODEL_PR)
+        return launch_batch_t<L, LBM_MODEL_PR, S>(check, descs, block_dom, nblocks, phase, partials, st);
+    return launch_batch_t<L, LBM_MODEL_IR, S>(check, descs, block_dom, nblocks, phase, partials, st);
+}
+
+template <class L>
+cudaError_t launch_batch_lat(int model, int storage, bool check, const BatchDesc* descs,
+                             const int* block_dom, int nblocks, int phase, double* partials,
+                             cudaStream_t st) {
+    switch (storage) {
+    case LBM_F32: return launch_batch_model<L, float>(model, check, descs, block_dom, nblocks, phase, partials, st);
+    case LBM_F64: return launch_batch_model<L, double>(model, check, descs, block_dom, nblocks, phase, partials, st);
+    case LBM_F16_OFS: return launch_batch_model<L, __half>(model, check, descs, block_dom, nblocks, phase, partials, st);
+    case LBM_BF16_OFS: return launch_batch_model<L, __nv_bfloat16>(model, check, descs, block_dom, nblocks, phase, partials, st);
+    default: return cudaErrorNotSupported;
+    }
+}
+
 template <class L>
 cudaError_t launch_links_lat(const KParams& kp, const uint8_t* mask, uint32_t* links,
                              cudaStream_t st) {
@@ -898,4 +1018,10 @@ template <class L> void lattice_table(int* c, double* w) {
         return launch_convert_lat<L>(storage, to_device, kp, q, f, plane_buf, st);              \
     }                                                                                           \
     void lattice_table_##L(int* c, double* w) { lattice_table<L>(c, w); }                       \
+    cudaError_t launch_step_batch_##L(int model, int storage, bool check, const BatchDesc* descs,\
+                                      const int* block_dom, int nblocks, int phase,            \
+                                      double* partials, cudaStream_t st) {                      \
+        return launch_batch_lat<L>(model, storage, check, descs, block_dom, nblocks, phase,     \
+                                   partials, st);                                               \
+    }                                                                                           \
     }

@@ -22,10 +22,11 @@
 
 #include "../../include/bingham_lbm.h"
 #include "lbm_internal.h"
+#include "solver.h"
 
 using namespace blbm;
 
-namespace {
+namespace blbm {
 
 thread_local std::string g_err;
 
@@ -64,12 +65,6 @@ size_t arith_bytes(int storage) { return storage == LBM_F64 ? 8 : 4; }
 bool storage_built(int storage) { return storage_bytes(storage) != 0; }
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
-
-struct Layout {
-    int64_t plane;
-    size_t off_f[2], off_links, off_tau, off_usnap, off_partials, off_stats, off_mask, total;
-    int nparts;
-};
 
 Layout make_layout(int lat, int nx, int ny, int nz, const lbm_params& p) {
     Layout L{};
@@ -122,36 +117,7 @@ lbm_status validate(int lat, int nx, int ny, int nz, const uint8_t* mask, const 
     return LBM_OK;
 }
 
-}  // namespace
-
-struct lbm_solver {
-    int lat = 0, Q = 0, D = 0, nx = 0, ny = 0, nz = 0;
-    int ncells = 0;
-    int64_t nfluid = 0;
-    lbm_params p{};
-    KParams kp{};
-    Layout lay{};
-    cudaStream_t stream = nullptr;
-    cudaStream_t cap_stream = nullptr;
-    int device = 0;
-    bool owns = false;
-    char* base = nullptr;
-    void* f[2] = {nullptr, nullptr};
-    uint32_t* links = nullptr;
-    void* tau = nullptr;
-    void* usnap = nullptr;
-    double* partials = nullptr;
-    double* stats = nullptr;
-    double* host_stats = nullptr;   // pinned, kNumStats doubles of the last check step
-    double* scratch = nullptr;      // lazily allocated: 4 x ncells doubles
-    int cur = 0;
-    int64_t steps = 0;
-    int64_t checks = 0;
-    int64_t last_check = -1;
-    bool poisoned = false;
-    cudaGraphExec_t graph[2] = {nullptr, nullptr};
-    int graph_len = 64;
-};
+}  // namespace blbm
 
 namespace {
 

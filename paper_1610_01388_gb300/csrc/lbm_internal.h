@@ -47,6 +47,8 @@ struct StepArgs {
 
 enum ReduceMode { kReduceFlow = 0, kReduceTotals = 1 };
 
+struct BatchDesc;   // per-domain descriptor of a batched launch (kernels.cuh)
+
 // Per-lattice launchers (defined in kern_<lattice>.cu).
 #define BLBM_DECLARE_LAUNCHERS(L)                                                              \
     cudaError_t launch_step_##L(int model, int storage, bool check, const KParams& kp,          \
@@ -61,7 +63,10 @@ enum ReduceMode { kReduceFlow = 0, kReduceTotals = 1 };
                                   cudaStream_t st);                                             \
     cudaError_t launch_convert_##L(int storage, bool to_device, const KParams& kp, int q,       \
                                    void* f, double* plane_buf, cudaStream_t st);                \
-    void lattice_table_##L(int* c, double* w);
+    void lattice_table_##L(int* c, double* w);                                                  \
+    cudaError_t launch_step_batch_##L(int model, int storage, bool check,                       \
+                                      const struct BatchDesc* descs, const int* block_dom,      \
+                                      int nblocks, int phase, double* partials, cudaStream_t st);
 
 BLBM_DECLARE_LAUNCHERS(D2Q9)
 BLBM_DECLARE_LAUNCHERS(D3Q15)

@@ -1,0 +1,56 @@
+// Internal definition of a solver handle, shared by the single-domain C ABI
+// (lbm_api.cu) and the batched runtime (lbm_batch.cu).  Not part of the ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "../../include/bingham_lbm.h"
+#include "lbm_internal.h"
+
+namespace blbm {
+
+// Device memory layout of one solver (offsets into one allocation).
+struct Layout {
+    int64_t plane;
+    size_t off_f[2], off_links, off_tau, off_usnap, off_partials, off_stats, off_mask, total;
+    int nparts;
+};
+
+lbm_status fail(lbm_status st, const char* fmt, ...);
+int lattice_q(int lat);
+size_t storage_bytes(int storage);
+size_t arith_bytes(int storage);
+
+}  // namespace blbm
+
+struct lbm_solver {
+    int lat = 0, Q = 0, D = 0, nx = 0, ny = 0, nz = 0;
+    int ncells = 0;
+    int64_t nfluid = 0;
+    lbm_params p{};
+    blbm::KParams kp{};
+    blbm::Layout lay{};
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    int device = 0;
+    bool owns = false;
+    char* base = nullptr;
+    void* f[2] = {nullptr, nullptr};   // population buffers; f[cur] is the state
+    uint32_t* links = nullptr;
+    void* tau = nullptr;
+    void* usnap = nullptr;
+    double* partials = nullptr;
+    double* stats = nullptr;           // then two u32 rounding counters
+    double* host_stats = nullptr;      // pinned, kNumStats doubles of the last check step
+    double* scratch = nullptr;         // lazily allocated: 4 x ncells doubles
+    int cur = 0;
+    int64_t steps = 0;
+    int64_t checks = 0;
+    int64_t last_check = -1;
+    bool poisoned = false;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    int graph_len = 64;
+};

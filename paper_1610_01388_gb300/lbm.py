@@ -35,7 +35,12 @@ EXPORTED = ["lbm_params_default", "lbm_lattice_info", "lbm_workspace_bytes", "lb
             "lbm_create_with_workspace", "lbm_step", "lbm_sync", "lbm_fields", "lbm_fields_device",
             "lbm_flowrate", "lbm_totals", "lbm_residual", "lbm_set_populations",
             "lbm_get_populations", "lbm_set_tau", "lbm_get_tau", "lbm_get_info", "lbm_destroy",
-            "lbm_last_error", "lbm_status_string"]
+            "lbm_last_error", "lbm_status_string", "lbm_flowrate_noalloc",
+            "lbm_batch_create", "lbm_batch_add", "lbm_batch_remove", "lbm_batch_step",
+            "lbm_batch_domain_status", "lbm_batch_solver", "lbm_batch_usage", "lbm_batch_destroy",
+            "lbm_server_create", "lbm_server_submit", "lbm_server_advance", "lbm_server_result",
+            "lbm_server_fields", "lbm_server_pending", "lbm_server_now", "lbm_server_destroy"]
+LBM_REQ_QUEUED, LBM_REQ_RUNNING, LBM_REQ_CONVERGED, LBM_REQ_CAPPED, LBM_REQ_FAILED = range(5)
 
 
 class LbmError(RuntimeError):
@@ -59,6 +64,26 @@ class lbm_info(ctypes.Structure):
                 ("steps_done", ctypes.c_int64), ("model", ctypes.c_int32),
                 ("storage", ctypes.c_int32), ("bytes_per_fluid_update", ctypes.c_double),
                 ("device_bytes", ctypes.c_size_t)]
+
+
+class lbm_domain_status(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int64), ("checks", ctypes.c_int64),
+                ("residual", ctypes.c_double), ("flow_x", ctypes.c_double),
+                ("nonfinite", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+class lbm_request(ctypes.Structure):
+    _fields_ = [("lattice", ctypes.c_int32), ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+                ("nz", ctypes.c_int32), ("solid_mask", ctypes.c_void_p), ("params", lbm_params),
+                ("tolerance", ctypes.c_double), ("max_steps", ctypes.c_int64),
+                ("keep_fields", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+class lbm_result(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int32), ("pad", ctypes.c_int32), ("steps", ctypes.c_int64),
+                ("fluid_cells", ctypes.c_int64), ("residual", ctypes.c_double),
+                ("flow_x", ctypes.c_double), ("t_submit", ctypes.c_double),
+                ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double)]
 
 
 _lib = None
@@ -97,13 +122,28 @@ def library():
             "lbm_get_tau": [vp, vp],
             "lbm_get_info": [vp, P(lbm_info)],
             "lbm_flowrate_noalloc": [vp, i32, vp],
+            "lbm_batch_create": [P(vp), sz, i32, vp],
+            "lbm_batch_add": [vp, i32, i32, i32, i32, vp, P(lbm_params), P(i64)],
+            "lbm_batch_remove": [vp, i64],
+            "lbm_batch_step": [vp, i64],
+            "lbm_batch_domain_status": [vp, i64, P(lbm_domain_status)],
+            "lbm_batch_solver": [vp, i64, P(vp)],
+            "lbm_batch_usage": [vp, P(sz), P(i64), P(i64)],
+            "lbm_server_create": [P(vp), sz, i32, vp],
+            "lbm_server_submit": [vp, P(lbm_request), P(i64)],
+            "lbm_server_advance": [vp, i64, P(i32)],
+            "lbm_server_result": [vp, i64, P(lbm_result)],
+            "lbm_server_fields": [vp, i64, vp, vp, vp, vp],
+            "lbm_server_pending": [vp, P(i64), P(i64), P(sz)],
+            "lbm_server_now": [vp, P(d)],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
             fn.argtypes = args
             fn.restype = ctypes.c_int
-        lib.lbm_destroy.argtypes = [vp]
-        lib.lbm_destroy.restype = None
+        for name in ("lbm_destroy", "lbm_batch_destroy", "lbm_server_destroy"):
+            getattr(lib, name).argtypes = [vp]
+            getattr(lib, name).restype = None
         lib.lbm_last_error.restype = ctypes.c_char_p
         lib.lbm_status_string.restype = ctypes.c_char_p
         lib.lbm_status_string.argtypes = [ctypes.c_int]
@@ -353,3 +393,135 @@ class Solver:
 
     def __exit__(self, *exc):
         self.close()
+
+
+# --- batched stepping ---------------------------------------------------------
+
+class Batch:
+    """Many resident domains stepped together (lbm_batch_*)."""
+
+    def __init__(self, budget_bytes, check_every=100, stream=None):
+        self.h = ctypes.c_void_p()
+        _check(library().lbm_batch_create(ctypes.byref(self.h), int(budget_bytes),
+                                          int(check_every), ctypes.c_void_p(stream or 0)))
+
+    def add(self, lattice, mask, **params):
+        mask = np.ascontiguousarray(mask, np.uint8)
+        if mask.ndim == 2:
+            mask = mask[None]
+        nz, ny, nx = mask.shape
+        p = lbm_params_default(**params)
+        i = ctypes.c_int64()
+        _check(library().lbm_batch_add(self.h, _lat(lattice), nx, ny, nz, _ptr(mask),
+                                       ctypes.byref(p), ctypes.byref(i)))
+        return i.value
+
+    def try_add(self, lattice, mask, **params):
+        """Domain id, or None if the budget is exhausted (LBM_EBUSY)."""
+        try:
+            return self.add(lattice, mask, **params)
+        except LbmError as e:
+            if e.status == LBM_EBUSY:
+                return None
+            raise
+
+    def remove(self, dom):
+        _check(library().lbm_batch_remove(self.h, int(dom)))
+
+    def step(self, n):
+        _check(library().lbm_batch_step(self.h, int(n)))
+
+    def status(self, dom):
+        st = lbm_domain_status()
+        _check(library().lbm_batch_domain_status(self.h, int(dom), ctypes.byref(st)))
+        return st
+
+    def solver(self, dom):
+        """Borrowed lbm_solver handle (for lbm_fields, lbm_flowrate, ...)."""
+        s = ctypes.c_void_p()
+        _check(library().lbm_batch_solver(self.h, int(dom), ctypes.byref(s)))
+        return s
+
+    def usage(self):
+        b, d, c = ctypes.c_size_t(), ctypes.c_int64(), ctypes.c_int64()
+        _check(library().lbm_batch_usage(self.h, ctypes.byref(b), ctypes.byref(d),
+                                         ctypes.byref(c)))
+        return b.value, d.value, c.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            library().lbm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# --- serving ----------------------------------------------------------------------
+
+class Server:
+    """Continuous-batching server of independent solves (lbm_server_*)."""
+
+    def __init__(self, budget_bytes, check_every=100, stream=None):
+        self.h = ctypes.c_void_p()
+        _check(library().lbm_server_create(ctypes.byref(self.h), int(budget_bytes),
+                                           int(check_every), ctypes.c_void_p(stream or 0)))
+
+    def submit(self, lattice, mask, tolerance=1e-6, max_steps=100000, keep_fields=False,
+               **params):
+        mask = np.ascontiguousarray(mask, np.uint8)
+        if mask.ndim == 2:
+            mask = mask[None]
+        nz, ny, nx = mask.shape
+        r = lbm_request()
+        r.lattice, r.nx, r.ny, r.nz = _lat(lattice), nx, ny, nz
+        r.solid_mask = mask.ctypes.data
+        r.params = lbm_params_default(**params)
+        r.tolerance = float(tolerance)
+        r.max_steps = int(max_steps)
+        r.keep_fields = 1 if keep_fields else 0
+        i = ctypes.c_int64()
+        _check(library().lbm_server_submit(self.h, ctypes.byref(r), ctypes.byref(i)))
+        return i.value
+
+    def advance(self, nsteps):
+        c = ctypes.c_int32()
+        _check(library().lbm_server_advance(self.h, int(nsteps), ctypes.byref(c)))
+        return c.value
+
+    def result(self, rid):
+        r = lbm_result()
+        _check(library().lbm_server_result(self.h, int(rid), ctypes.byref(r)))
+        return r
+
+    def fields(self, rid, shape):
+        n = int(np.prod(shape))
+        out = np.empty((4, n), np.float64)
+        _check(library().lbm_server_fields(self.h, int(rid), _ptr(out[0]), _ptr(out[1]),
+                                           _ptr(out[2]), _ptr(out[3])))
+        return out[0].reshape(shape), out[1:].reshape((3,) + tuple(shape))
+
+    def pending(self):
+        q, r, b = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_size_t()
+        _check(library().lbm_server_pending(self.h, ctypes.byref(q), ctypes.byref(r),
+                                            ctypes.byref(b)))
+        return q.value, r.value, b.value
+
+    def now(self):
+        t = ctypes.c_double()
+        _check(library().lbm_server_now(self.h, ctypes.byref(t)))
+        return t.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            library().lbm_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
