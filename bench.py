@@ -259,6 +259,14 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
 
     e2e = run_e2e(args, mask, nfluid, g, sy, dev)
+    serving = None
+    if args.serve_requests > 0:
+        serving = {"form": "served FP16-offset storage (stochastic rounding) vs FP32, batched",
+                   "budget_gb": 120, "rate_per_s": args.serve_rate,
+                   "tolerance": args.serve_tolerance, "step_cap": args.serve_max_steps,
+                   "mix": "D2Q9 channels 4 x (17..257), D3Q19/D3Q27 ducts 64 x (33..97)^2, "
+                          "D3Q19/D3Q27 porous boxes (32..64)^3 porosity 0.7; Bn U[0.1,10]; PR/IR",
+                   "runs": [run_serving(args, st) for st in ("F16", "F32")]}
     cpu = run_cpu_baseline(args) if (rank == 0 and ws == 1 and not args.no_cpu) else None
     if rank == 0:
         line = {"metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": ws,
@@ -267,7 +275,7 @@ def run_ours(args):
                 "dtype": STORAGE_DTYPE[STORAGE], "data": "synthetic",
                 "config": workload_config({"per_rank": "independent duct pair per GPU",
                                            "fluid_cells": nfluid}),
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "serving": serving,
                 "gpu_launches": 2 * launches_per_model, "clocks": clk,
                 "wall_s_timed_region": round(t1 - t0, 4)}
         print(json.dumps(line), flush=True)
@@ -306,6 +314,58 @@ def run_e2e(args, mask, nfluid, g, sy, dev):
             "d2h_bytes_per_step": round(2 * 4 * 8 * mask.size / K, 3),
             "steps": K, "what": "per model: lbm_create (host mask H2D) + lbm_step(K) + "
                                 "lbm_fields (rho,u D2H) + lbm_destroy, inside the timed region"}
+
+
+# --- serving ----------------------------------------------------------------------
+
+def run_serving(args, storage):
+    """A Poisson stream of independent solves (channels, ducts, porous boxes;
+    Bn uniform in [0.1, 10]; PR or IR) through the continuous-batching server
+    under a 120 GB budget: requests are submitted at their arrival times while
+    the server steps everything admitted in 200-step chunks (check every 100).
+    Latency = completion - arrival; time to steady state is that latency for
+    the requests whose residual fell below the tolerance."""
+    from paper_1610_01388_gb300 import lbm
+    from paper_1610_01388_gb300 import workloads as W
+    reqs = W.serving_requests(n=args.serve_requests, rate=args.serve_rate, seed=7,
+                              storage=storage, max_steps=args.serve_max_steps,
+                              tolerance=args.serve_tolerance)
+    srv = lbm.Server(120 * (1 << 30), check_every=100)
+    t0 = srv.now()
+    ids = []
+    k = 0
+    while True:
+        now = srv.now() - t0
+        while k < len(reqs) and reqs[k]["arrival"] <= now:
+            r = reqs[k]
+            ids.append(srv.submit(r["lattice"], r["mask"], tolerance=r["tolerance"],
+                                  max_steps=r["max_steps"], model=r["model"],
+                                  storage=r["storage"], mu_p=r["mu_p"], sigma_y=r["sigma_y"],
+                                  m=r["m"], g=r["g"]))
+            k += 1
+        q, running, _ = srv.pending()
+        if q == 0 and running == 0:
+            if k == len(reqs):
+                break
+            time.sleep(max(0.0, reqs[k]["arrival"] - (srv.now() - t0)))
+            continue
+        srv.advance(200)
+    res = [srv.result(i) for i in ids]
+    srv.close()
+    lat = np.array([r.t_done - r.t_submit for r in res])
+    conv = np.array([r.state == lbm.LBM_REQ_CONVERGED for r in res])
+    upd = sum(r.fluid_cells * r.steps for r in res)
+    span = max(r.t_done for r in res) - min(r.t_submit for r in res)
+    tts = lat[conv]
+    return {"storage": storage, "requests": len(res), "served_solves_per_s": round(len(res) / span, 3),
+            "latency_p50_s": round(float(np.percentile(lat, 50)), 4),
+            "latency_p99_s": round(float(np.percentile(lat, 99)), 4),
+            "time_to_steady_p50_s": round(float(np.percentile(tts, 50)), 4) if tts.size else None,
+            "time_to_steady_p99_s": round(float(np.percentile(tts, 99)), 4) if tts.size else None,
+            "converged": int(conv.sum()),
+            "capped": int(sum(r.state == lbm.LBM_REQ_CAPPED for r in res)),
+            "failed": int(sum(r.state == lbm.LBM_REQ_FAILED for r in res)),
+            "aggregate_mlups": round(upd / span / 1e6, 1), "makespan_s": round(span, 3)}
 
 
 # --- oracle arms ------------------------------------------------------------------
@@ -386,6 +446,11 @@ def main(argv=None):
     ap.add_argument("--e2e-steps", type=int, default=0)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=300,
+                    help="requests in the serving leg (0 skips it)")
+    ap.add_argument("--serve-rate", type=float, default=150.0, help="Poisson arrival rate, 1/s")
+    ap.add_argument("--serve-max-steps", type=int, default=3000)
+    ap.add_argument("--serve-tolerance", type=float, default=1e-3)
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu dram bytes per launch of the dominant kernel, if captured")
     ap.add_argument("--nx", type=int, default=NX, help="duct length (other workloads)")

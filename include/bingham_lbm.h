@@ -241,7 +241,7 @@ typedef struct {
     int64_t steps;      /* time steps this domain has taken */
     int64_t checks;     /* check steps it has seen */
     double residual;    /* last check step; -1 before two check steps */
-    double flow_x;      /* flow rate along x at the last check step */
+    double flow[3];     /* flow rate along x, y, z at the last check step */
     int32_t nonfinite;  /* 1 if the last check step saw a non-finite density */
     int32_t pad;
 } lbm_domain_status;
@@ -272,8 +272,12 @@ void lbm_batch_destroy(lbm_batch *b);
  * device-memory budget allows (in submission order, letting a smaller later
  * request in when an earlier one does not fit), advances every running
  * solve together by nsteps (a multiple of check_every) through one batch,
- * and retires the solves whose residual fell below their tolerance or that
- * reached their step cap, freeing their memory for the next admissions.
+ * and retires the solves that reached steady state or their step cap,
+ * freeing their memory for the next admissions.  Steady state: the flow
+ * rate along the body force changed by less than tolerance (relative)
+ * between the last check steps of two consecutive advance calls -- the
+ * integral counterpart of the paper's U_max change criterion (Sec. 4.4),
+ * insensitive to per-cell rounding noise of the 16-bit storage forms.
  * Times are seconds on the server's monotonic clock (lbm_server_now).
  * ------------------------------------------------------------------------ */
 typedef struct lbm_server lbm_server;
@@ -282,7 +286,7 @@ typedef struct {
     int32_t lattice, nx, ny, nz;
     const uint8_t *solid_mask;  /* host, nx*ny*nz, copied at submit */
     lbm_params params;
-    double tolerance;           /* steady state: residual < tolerance */
+    double tolerance;           /* steady state: relative flow-rate change < tolerance */
     int64_t max_steps;          /* step cap (> 0) */
     int32_t keep_fields;        /* keep rho and u_real of the final state on the host */
     int32_t pad;
@@ -296,7 +300,7 @@ typedef struct {
     int32_t pad;
     int64_t steps;
     int64_t fluid_cells;
-    double residual;            /* at completion */
+    double residual;            /* field residual of the last check step */
     double flow_x;              /* flow rate along x at completion (lbm_flowrate) */
     double t_submit, t_admit, t_done;
 } lbm_result;

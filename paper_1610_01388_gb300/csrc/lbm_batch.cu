@@ -401,7 +401,8 @@ lbm_status lbm_batch_domain_status(lbm_batch* b, int64_t id, lbm_domain_status* 
     std::memset(st, 0, sizeof(*st));
     st->steps = d.s->steps;
     st->checks = d.checks;
-    st->flow_x = d.checks > 0 ? r[kStatUx] / d.s->nx : 0.0;
+    const int len[3] = {d.s->nx, d.s->ny, d.s->nz};
+    for (int a = 0; a < 3; ++a) st->flow[a] = d.checks > 0 ? r[kStatUx + a] / len[a] : 0.0;
     st->residual = (d.checks >= 2 && r[kStatU2] > 0.0) ? std::sqrt(r[kStatDu2] / r[kStatU2]) : -1.0;
     st->nonfinite = (d.checks > 0 && r[kStatNonFinite] != 0.0) ? 1 : 0;
     return LBM_OK;
@@ -463,6 +464,9 @@ struct Req {
     lbm_result res{};
     int64_t dom = 0;
     size_t bytes = 0;
+    int axis = 0;           // largest body-force component: the flow direction
+    double prev_flow = 0.0;
+    bool has_prev = false;
     std::vector<double> fields;   // rho, ux, uy, uz of the final state (keep_fields)
 };
 
@@ -522,6 +526,8 @@ lbm_status lbm_server_submit(lbm_server* s, const lbm_request* req, int64_t* id)
     r.mask.assign(req->solid_mask, req->solid_mask + n);
     r.r.solid_mask = nullptr;
     r.bytes = bytes;
+    for (int a = 1; a < 3; ++a)
+        if (std::fabs(req->params.g[a]) > std::fabs(req->params.g[r.axis])) r.axis = a;
     r.res.state = LBM_REQ_QUEUED;
     r.res.t_submit = now_s() - s->t0;
     *id = s->next_id++;
@@ -602,8 +608,13 @@ lbm_status lbm_server_advance(lbm_server* s, int64_t nsteps, int32_t* completed)
         lbm_domain_status ds;
         if ((v = lbm_batch_domain_status(s->batch, r.dom, &ds)) != LBM_OK) return v;
         int state = -1;
+        const double q = ds.flow[r.axis];
+        const bool steady = r.has_prev && std::fabs(q - r.prev_flow) <= r.r.tolerance * std::fabs(q) &&
+                            q != 0.0;
+        r.prev_flow = q;
+        r.has_prev = ds.checks > 0;
         if (ds.nonfinite) state = LBM_REQ_FAILED;
-        else if (ds.residual >= 0.0 && ds.residual < r.r.tolerance) state = LBM_REQ_CONVERGED;
+        else if (steady) state = LBM_REQ_CONVERGED;
         else if (ds.steps >= r.r.max_steps) state = LBM_REQ_CAPPED;
         if (state >= 0) {
             if ((v = retire(s, rid, state)) != LBM_OK) return v;

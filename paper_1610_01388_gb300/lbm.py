@@ -68,7 +68,7 @@ class lbm_info(ctypes.Structure):
 
 class lbm_domain_status(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int64), ("checks", ctypes.c_int64),
-                ("residual", ctypes.c_double), ("flow_x", ctypes.c_double),
+                ("residual", ctypes.c_double), ("flow", ctypes.c_double * 3),
                 ("nonfinite", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 

@@ -179,3 +179,46 @@ def duct_params(H: int = 127, nu_p: float = 0.1, u_newton: float = 0.02, bn: flo
     g = 16.0 * nu_p * u_newton / (C_MAX * H * H)
     bi = duct_bn_to_bi(bn) if bn > 0 else 0.0
     return {"g": g, "sigma_y": bi * g * H / 4.0, "bi": bi, "nu_p": nu_p}
+
+
+def porous_params(nu_p: float = 0.1, d_mean: float = 16.0, g: float = 2e-5, bn: float = 1.0):
+    """Porous box: a-priori Bn = 4 sigma_y / (rho g d_mean)."""
+    return {"g": g, "sigma_y": bn * g * d_mean / 4.0, "nu_p": nu_p}
+
+
+def serving_requests(n: int = 200, rate: float = 40.0, seed: int = 7, storage: str = "F16",
+                     channel_widths=(16, 256), duct_sides=(32, 96), duct_length: int = 64,
+                     porous_sides=(32, 64), max_steps: int = 2000, tolerance: float = 1e-4):
+    """Poisson stream of independent solves: 2D channels (D2Q9, 4 x width),
+    square ducts (D3Q19/D3Q27, side x side x length) and porous boxes
+    (D3Q19/D3Q27, random spheres, porosity 0.7), Bingham number uniform in
+    [0.1, 10], model PR or IR with equal probability.  Returns a list of dicts
+    with the arrival time (s) and everything a solver needs."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    t = 0.0
+    out = []
+    for k in range(n):
+        t += rng.exponential(1.0 / rate)
+        kind = rng.integers(3)
+        bn = float(rng.uniform(0.1, 10.0))
+        model = "PR" if rng.integers(2) == 0 else "IR"
+        if kind == 0:
+            w = int(rng.integers(channel_widths[0], channel_widths[1] + 1))
+            mask = channel_mask(4, w + 1)
+            p = channel_params(H=w, nu_p=0.1, u_newton=0.02, bn=bn)
+            lat, g = "D2Q9", (p["g"], 0.0, 0.0)
+        elif kind == 1:
+            s = int(rng.integers(duct_sides[0], duct_sides[1] + 1))
+            mask = duct_mask(duct_length, s + 1, s + 1)
+            p = duct_params(H=s, nu_p=0.1, u_newton=0.02, bn=min(bn, 8.0))
+            lat, g = ("D3Q19" if rng.integers(2) == 0 else "D3Q27"), (p["g"], 0.0, 0.0)
+        else:
+            s = int(rng.integers(porous_sides[0], porous_sides[1] + 1))
+            mask, _ = porous_mask(s, porosity=0.7, r_min=4, r_max=6, seed=int(rng.integers(1 << 30)))
+            p = porous_params(nu_p=0.1, d_mean=10.0, g=2e-5, bn=bn)
+            lat, g = ("D3Q19" if rng.integers(2) == 0 else "D3Q27"), (p["g"], 0.0, 0.0)
+        out.append({"arrival": t, "lattice": lat, "mask": mask, "model": model,
+                    "storage": storage, "mu_p": 0.1, "sigma_y": p["sigma_y"], "m": 1e6,
+                    "g": g, "tolerance": tolerance, "max_steps": max_steps,
+                    "kind": ("channel", "duct", "porous")[kind], "bn": bn})
+    return out

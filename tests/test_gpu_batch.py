@@ -1,8 +1,9 @@
 """Batched stepping (lbm_batch_*) and serving (lbm_server_*) on the GPU.
 
-* every domain of a mixed batch ends bitwise equal (FP32 / FP64 storage) to the
-  same domain stepped alone with lbm_step: one launch per (lattice, model,
-  storage) group runs the same per-cell arithmetic;
+* every domain of a mixed batch ends equal to round-off to the same domain
+  stepped alone with lbm_step: one launch per (lattice, model, storage) group
+  runs the same per-cell code (the two kernels are compiled separately, so
+  fused multiply-adds may be placed differently);
 * the per-domain check-step residual equals the single-solver one;
 * admission respects the byte budget; domains added or removed mid-run keep
   the others exact;
@@ -66,7 +67,7 @@ def test_mixed_batch_matches_single_domain_runs():
         r, at, qx = ref.residual()
         assert st.steps == n and at == 300
         assert abs(st.residual - r) <= max(tol, 1e-12) * 10 * abs(r)
-        assert abs(st.flow_x - qx) <= tol * abs(qx)
+        assert abs(st.flow[0] - qx) <= tol * abs(qx)
         ref.close()
     b.close()
 
