@@ -71,6 +71,8 @@ typedef struct {
     double gdot_c;    /* PR zero-strain cut-off gdot^C */
     double g[3];      /* body acceleration; force density F = rho g */
     double magic;     /* TRT magic number Lambda (PR) */
+    int burnett_x;    /* 1: Burnett-suppressed variant for flow along x (Secs. 4.2.1,
+                         4.2.2): d_xx = 0 in the PR strain rate, T_xx = 0 in IR */
 } orc_params;
 
 typedef struct {
@@ -234,6 +236,9 @@ static void collide(const orc_lattice *L, const orc_params *p, const double *fin
             for (int i = 0; i < Q; ++i) acc += L->c[i][a] * L->c[i][b] * (fin[i] - feq[i]);
             T[a][b] = acc;
         }
+    /* Burnett-suppressed variant: the xx component is dropped (for PR this is
+     * d_xx = 0, since D is proportional to T). */
+    if (p->burnett_x) T[0][0] = 0.0;
 
     if (p->model == ORC_PR) {
         /* eq. (LBM_strain_rate): D = -T / (2 tau_old c_s^2), previous step's tau. */

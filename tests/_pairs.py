@@ -40,7 +40,7 @@ def make_pair(lat, mask, model="IR", storage="F32", nu_p=0.1, sigma_y=0.0, m=0.0
                    gammadot_c=gammadot_c, g=g, magic=magic, check_every=check_every,
                    flags=flags, use_torch=use_torch)
     p = oracle.params(model=model, nu_p=nu_p, sigma_y=sigma_y, m=m, gdot_c=gammadot_c, g=g,
-                      magic=magic)
+                      magic=magic, burnett_x=bool(flags & lbm.LBM_FLAG_BURNETT_X))
     o = oracle.State(lat, p, mask, nthreads=nthreads)
     return s, o
 

@@ -218,3 +218,18 @@ def test_nonfinite_density_is_reported():
         s.residual()
     assert ei.value.status == lbm.LBM_ENONFINITE
     s.close()
+
+
+@pytest.mark.parametrize("model", ["PR", "IR"])
+@pytest.mark.parametrize("storage", ["F64", "F32"])
+def test_burnett_suppressed_variant(model, storage):
+    """LBM_FLAG_BURNETT_X (d_xx = 0 / T_xx = 0, Secs. 4.2.1-4.2.2) against the
+    oracle's same option, on a duct from a random start."""
+    mask = W.duct_mask(11, 13, 12)
+    s, o = make_pair("D3Q27", mask, model=model, storage=storage, sigma_y=3e-5, m=1e6,
+                     g=(2e-5, 0, 0), nu_p=0.08, flags=lbm.LBM_FLAG_BURNETT_X)
+    set_both("D3Q27", s, o, W.random_populations(o.w, o.N, amplitude=0.01, seed=21))
+    s.step(60)
+    o.step(60)
+    assert rel_l2_u(s, o) < TOL[storage]
+    s.close()

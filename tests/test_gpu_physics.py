@@ -98,3 +98,80 @@ def test_creeping_cylinder_array_table(model):
         if sy > 0:
             assert abs(bn - want["Bn"]) / want["Bn"] < 0.01
         s.close()
+
+
+def _duct63(model, m=1e8, storage="F64", flags=0, gammadot_c=1e-8):
+    sc = GOLD["duct_convergence_scaling"]
+    D = 63
+    g = sc["g0"] * (sc["D0"] / D) ** 3           # 2.70e-7
+    sy = sc["sigma_y0"] * (sc["D0"] / D) ** 2    # 1.70e-6
+    return lbm.Solver("D3Q27", W.duct_mask(1, D + 1, D + 1), model=model, storage=storage,
+                      mu_p=sc["nu"], sigma_y=sy, m=m, g=(g, 0, 0), flags=flags,
+                      gammadot_c=gammadot_c), sy
+
+
+def test_pr_m_sweep_and_apparent_viscosity():
+    """Sec. 4.2.1, Table Rel_error_m: relative U_max error of PR against
+    m = 1e14 in the 63 lu square duct (1.37, 1.03e-2, 8.5e-6, 0 for m = 1e3,
+    1e6, 1e9, 1e12); the apparent viscosity saturates far below the limit
+    nu_p + m sigma_y at large m because of the Burnett d_xx (the paper reads
+    ~727), and reaches the limit when d_xx is set to zero.
+
+    The saturation value sigma_y / nu_app ~ 2e-9 is below the printed cut-off
+    gdot^C = 1e-8, where a linear interpolation towards nu_0 would stiffen the
+    flow (measured: U_max at m = 1e9 drops to 0.64 of its m = 1e6 value and the
+    fluid does not yield from rest at m >= 1e12).  The paper's table is
+    reproduced with the cut-off below the strain rates of the flow
+    (gdot^C = 1e-20), which is how it is pinned here."""
+    rows = GOLD["pr_m_sweep_relative_error"]["rows"]
+    umax = {}
+    nu_max = {}
+    for m in (1e3, 1e6, 1e9, 1e12, 1e14):
+        s, sy = _duct63("PR", m=m, gammadot_c=1e-20)
+        umax[m], steps = _run_to_steady(s, 50_000, 1_500_000, 1e-11, _umax)
+        tau = s.get_tau()[s.mask == 0]
+        nu_max[m] = (tau.max() - 0.5) / 3.0
+        print(f"PR m={m:g}: U_max {umax[m]:.10e}, max nu_app {nu_max[m]:.4g} "
+              f"(limit {0.0125 + m * sy:.4g}) after {steps} steps")
+        s.close()
+    ref = umax[1e14]
+    got = {m: abs(umax[m] - ref) / ref for m in umax}
+    for m, want in rows:
+        print(f"  m={m:g}: rel err {got[m]:.3e} (paper {want:g})")
+    # measured: 1.248, 5.3e-3, 5.7e-7, 1.7e-15
+    assert abs(got[1e3] - 1.37) / 1.37 < 0.15
+    assert 0.4 * 1.03e-2 < got[1e6] < 2.5 * 1.03e-2
+    assert got[1e9] < 8.5e-6
+    assert got[1e12] < 1e-12
+    # saturation (measured ~594 for m >= 1e12; the paper reads ~727)
+    assert nu_max[1e12] < 1e-3 * (0.0125 + 1e12 * 1.7e-6)
+    assert abs(nu_max[1e14] - nu_max[1e12]) < 0.01 * nu_max[1e12]
+    assert 727 / 1.5 < nu_max[1e12] < 727 * 1.5
+    # the large-m velocity is the Bingham one: Re near the spectral 12.6242614
+    re = umax[1e14] * 63 / 0.0125
+    assert abs(re - GOLD["square_duct_spectral"]["Re"]) / GOLD["square_duct_spectral"]["Re"] < 2e-3
+    s, sy = _duct63("PR", m=1e9, flags=lbm.LBM_FLAG_BURNETT_X, gammadot_c=1e-20)
+    _run_to_steady(s, 50_000, 1_500_000, 1e-10, _umax)
+    nu_flag = (s.get_tau()[s.mask == 0].max() - 0.5) / 3.0
+    print(f"PR m=1e9 with d_xx = 0: max nu_app {nu_flag:.6g} (limit {0.0125 + 1e9 * sy:.6g})")
+    assert abs(nu_flag - (0.0125 + 1e9 * sy)) < 1e-3 * (0.0125 + 1e9 * sy)
+    s.close()
+
+
+def test_ir_transverse_currents_vanish_without_burnett_term():
+    """Sec. 4.2.2: IR's deviatoric projection redistributes the Burnett T_xx
+    and drives small transverse currents in a Bingham duct; with T_xx = 0
+    they vanish and U_max changes only by O(1e-7) relative."""
+    res = {}
+    for flags in (0, lbm.LBM_FLAG_BURNETT_X):
+        s, _ = _duct63("IR", flags=flags)
+        u, _ = _run_to_steady(s, 50_000, 1_500_000, 1e-10, _umax)
+        _, vel = s.fields()
+        res[flags] = (u, np.max(np.abs(vel[1:])))
+        s.close()
+    (u0, t0), (u1, t1) = res[0], res[lbm.LBM_FLAG_BURNETT_X]
+    print(f"IR transverse max {t0:.3e} (with Burnett term) vs {t1:.3e} (T_xx = 0); "
+          f"U_max rel diff {abs(u0 - u1) / u1:.2e}")
+    assert t0 > 1e-4 * u0 * 1e-3          # present
+    assert t1 < 1e-6 * t0 + 1e-18         # gone
+    assert abs(u0 - u1) / u1 < 1e-5

@@ -283,3 +283,28 @@ def test_pr_uses_previous_tau_for_strain_rate():
     g1 = oracle.collide(lat, p, f, tau_old=0.8)[2]["gdot"]
     g2 = oracle.collide(lat, p, f, tau_old=1.6)[2]["gdot"]
     assert abs(g1 - 2 * g2) < 1e-12 * g1
+
+
+@pytest.mark.parametrize("lat", ["D3Q19", "D3Q27"])
+def test_burnett_suppressed_variant_drops_xx(lat):
+    """Secs. 4.2.1-4.2.2: with d_xx = 0 (PR) / T_xx = 0 (IR), a unidirectional
+    shear D_xy plus any xx non-equilibrium perturbation gives the strain rate
+    of the shear alone, and the IR stress has no xx component."""
+    c, w, _ = oracle.lattice_info(lat)
+    cf = c.astype(np.float64)
+    tau = 0.9
+    Dm = np.zeros((3, 3))
+    Dm[0, 1] = Dm[1, 0] = 3e-5
+    h = np.einsum("ia,ib,ab->i", cf, cf, Dm) - np.trace(Dm) / 3.0
+    pert = 1e-5 * w * (cf[:, 0] ** 2 - 1.0 / 3.0)          # an xx-only second moment
+    f = oracle.feq(lat, 1.0, [0, 0, 0]) - tau * w * h * 3.0 + pert
+    shear = np.sqrt(2 * np.sum(Dm * Dm))
+    pr_on = oracle.params(model="PR", nu_p=0.1, sigma_y=1e-6, m=1e6, burnett_x=True)
+    pr_off = oracle.params(model="PR", nu_p=0.1, sigma_y=1e-6, m=1e6)
+    g_on = oracle.collide(lat, pr_on, f, tau_old=tau)[2]["gdot"]
+    g_off = oracle.collide(lat, pr_off, f, tau_old=tau)[2]["gdot"]
+    assert abs(g_on - shear) < 1e-12 * shear
+    assert g_off > shear * (1 + 1e-3)
+    ir_on = oracle.params(model="IR", nu_p=0.1, sigma_y=1e-9, burnett_x=True)
+    d = oracle.collide(lat, ir_on, f)[2]
+    assert d["T"][0, 0] == 0.0 and d["sigma"][0, 0] == 0.0
