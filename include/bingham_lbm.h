@@ -219,6 +219,22 @@ lbm_status lbm_flowrate_noalloc(lbm_solver *s, int axis, double *q_device);
 void lbm_destroy(lbm_solver *s);
 
 /* ------------------------------------------------------------------------
+ * Tuning table (no counterpart in the paper): threads per block (128, 256 or
+ * 512) of the plain step kernel for a (lattice, model, storage, size class),
+ * size class = floor(log2(cells)).  Process-wide; entries default to 256.
+ * Solvers adopt a changed entry at their next lbm_step (re-capturing their
+ * graphs).  Check steps always use 256 threads, so flow rates and residuals
+ * do not depend on the tuning.  The project's autotuner
+ * (paper_1610_01388_gb300.autotune) measures the candidates and fills it.
+ * ------------------------------------------------------------------------ */
+lbm_status lbm_tuning_set(lbm_lattice lat, int32_t model, int32_t storage, int32_t size_class,
+                          int32_t block);
+/* Block used for a problem of `cells` cells, and its size class. */
+lbm_status lbm_tuning_get(lbm_lattice lat, int32_t model, int32_t storage, int64_t cells,
+                          int32_t *block, int32_t *size_class);
+lbm_status lbm_tuning_clear(void);
+
+/* ------------------------------------------------------------------------
  * Batched stepping of many resident domains (no counterpart in the paper: a
  * throughput form for many small, independent solves).
  *

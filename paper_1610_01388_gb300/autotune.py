@@ -1,0 +1,89 @@
+"""Autotuner for the step kernel's block size.
+
+For a (lattice, model, storage, size class) it builds a synthetic square duct
+with about 2**size_class cells, times every candidate block size (128, 256,
+512 threads) for a few hundred steps with CUDA events on the solver's stream
+(after a warm-up that also captures the CUDA graphs), takes the fastest, and
+writes it into the library's tuning table (lbm_tuning_set).  Results are
+cached in a JSON file keyed by the GPU name so later processes skip the
+measurement (``load``).  All timing goes through the C ABI; the tuned solver
+arithmetic is the same for every block size, only the launch shape changes.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+
+from . import lbm
+from . import workloads as W
+
+CANDIDATES = (128, 256, 512)
+
+
+def _gpu_name():
+    import torch
+    return torch.cuda.get_device_name(torch.cuda.current_device())
+
+
+def _duct_for(lattice, cells):
+    if lattice == "D2Q9":
+        ny = max(8, int(math.sqrt(cells)))
+        nx = max(4, cells // ny)
+        return W.channel_mask(nx, ny)
+    side = max(8, int(round((cells / 2) ** (1 / 3))))
+    return W.duct_mask(max(4, cells // (side * side)), side, side)
+
+
+def measure(lattice, model, storage, size_class, steps=300, warmup=70):
+    """Average step time (s) of every candidate block size."""
+    import torch
+    cells = 1 << size_class
+    mask = _duct_for(lattice, cells)
+    out = {}
+    for block in CANDIDATES:
+        lbm.lbm_tuning_set(lattice, model, storage, size_class, block)
+        s = lbm.Solver(lattice, mask, model=model, storage=storage, mu_p=0.1, sigma_y=1e-6,
+                       m=1e6, g=(1e-6, 0.0, 0.0), use_torch=True)
+        s.step(warmup)
+        st = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        s.step(steps)
+        e1.record(st)
+        torch.cuda.synchronize()
+        out[block] = e0.elapsed_time(e1) / 1e3 / steps
+        s.close()
+    return out
+
+
+def tune(lattice, model, storage, cells, cache=None, steps=300):
+    """Tune the size class of `cells`; returns (best block, {block: seconds})."""
+    _, cls = lbm.lbm_tuning_get(lattice, model, storage, cells)
+    times = measure(lattice, model, storage, cls, steps=steps)
+    best = min(times, key=times.get)
+    lbm.lbm_tuning_set(lattice, model, storage, cls, best)
+    if cache:
+        data = _read(cache)
+        data.setdefault(_gpu_name(), {})[f"{lattice}/{model}/{storage}/{cls}"] = {
+            "block": best, "seconds_per_step": times}
+        with open(cache, "w") as fh:
+            json.dump(data, fh, indent=1, sort_keys=True)
+    return best, times
+
+
+def _read(path):
+    if path and os.path.exists(path):
+        with open(path) as fh:
+            return json.load(fh)
+    return {}
+
+
+def load(cache):
+    """Apply cached decisions for this GPU; returns how many were applied."""
+    n = 0
+    for key, v in _read(cache).get(_gpu_name(), {}).items():
+        lat, model, storage, cls = key.split("/")
+        lbm.lbm_tuning_set(lat, model, storage, int(cls), int(v["block"]))
+        n += 1
+    return n

@@ -601,15 +601,19 @@ __device__ __forceinline__ void cell_step(const KParams& kp, const Coef<typename
     }
 }
 
-template <class L, int MODEL, class S, bool CHECK>
-__global__ void __launch_bounds__(kBlock, step_min_blocks<MODEL>())
+// BLOCK: threads per block, chosen per (lattice, model, storage, size class)
+// by the tuning table; check steps always run with kBlock so their reduction
+// order does not depend on the tuning.
+template <class L, int MODEL, class S, bool CHECK, int BLOCK = kBlock>
+__global__ void __launch_bounds__(BLOCK, step_min_blocks<MODEL>())
 k_step(const KArgs a, const SrcPlanes<S> src, const DstPlanes<S> dst,
        const uint32_t* __restrict__ links, typename Store<S>::R* __restrict__ tau,
        typename Store<S>::R* __restrict__ usnap, double* __restrict__ partials,
        uint32_t* __restrict__ rng_ctr, int parity) {
+    static_assert(!CHECK || BLOCK == kBlock, "check steps use the fixed block size");
     using R = typename Store<S>::R;
     const KParams& kp = a.kp;
-    const int idx = blockIdx.x * kBlock + threadIdx.x;
+    const int idx = blockIdx.x * BLOCK + threadIdx.x;
     const bool inside = idx < kp.ncells;
     uint32_t rnd = 0u;
     if constexpr (Store<S>::kStochastic) {
@@ -852,12 +856,19 @@ cudaError_t launch_step_t(bool check, const KParams& kp, const StepArgs& s, cuda
     const int grid = step_grid(kp.ncells);
     const SrcPlanes<S> src = src_planes<L, S>(s.fsrc, kp.plane);
     const DstPlanes<S> dst = dst_planes<L, S>(s.fdst, kp.plane);
-    if (check)
+    if (check) {
         k_step<L, MODEL, S, true><<<grid, kBlock, 0, st>>>(
             a, src, dst, s.links, (R*)s.tau, (R*)s.usnap, s.partials, s.rng_ctr, s.parity);
-    else
+    } else if (s.block == 128) {
+        k_step<L, MODEL, S, false, 128><<<(kp.ncells + 127) / 128, 128, 0, st>>>(
+            a, src, dst, s.links, (R*)s.tau, (R*)s.usnap, s.partials, s.rng_ctr, s.parity);
+    } else if (s.block == 512) {
+        k_step<L, MODEL, S, false, 512><<<(kp.ncells + 511) / 512, 512, 0, st>>>(
+            a, src, dst, s.links, (R*)s.tau, (R*)s.usnap, s.partials, s.rng_ctr, s.parity);
+    } else {
         k_step<L, MODEL, S, false><<<grid, kBlock, 0, st>>>(
             a, src, dst, s.links, (R*)s.tau, (R*)s.usnap, s.partials, s.rng_ctr, s.parity);
+    }
     return cudaGetLastError();
 }
 

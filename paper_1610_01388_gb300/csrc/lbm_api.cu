@@ -15,6 +15,8 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
+#include <map>
 #include <mutex>
 #include <new>
 #include <string>
@@ -151,6 +153,7 @@ cudaError_t launch_step(lbm_solver* s, bool check, cudaStream_t st) {
     a.partials = s->partials;
     a.rng_ctr = (uint32_t*)(s->stats + 2 * kNumStats);
     a.parity = s->cur;
+    a.block = s->block;
     switch (s->lat) {
     case LBM_D2Q9: return launch_step_D2Q9(s->p.model, s->p.storage, check, s->kp, a, st);
     case LBM_D3Q15: return launch_step_D3Q15(s->p.model, s->p.storage, check, s->kp, a, st);
@@ -475,10 +478,91 @@ lbm_status lbm_create_with_workspace(lbm_solver** out, lbm_lattice lat, int nx, 
     return create_impl(out, lat, nx, ny, nz, solid_mask, p, cuda_stream, workspace, workspace_bytes);
 }
 
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Tuning table: threads per block of the plain step kernel per (lattice,
+// model, storage, size class = floor(log2 cells)); filled by the autotuner
+// through lbm_tuning_set, read by every solver before it steps.
+namespace {
+
+std::mutex g_tune_mu;
+std::map<uint64_t, int> g_tune;
+std::atomic<uint64_t> g_tune_version{0};
+
+int size_class(int64_t cells) {
+    int c = 0;
+    while ((int64_t(1) << (c + 1)) <= cells && c < 62) ++c;
+    return c;
+}
+
+uint64_t tune_key(int lat, int model, int storage, int cls) {
+    return ((uint64_t)lat << 24) | ((uint64_t)model << 16) | ((uint64_t)storage << 8) | (uint64_t)cls;
+}
+
+int tune_lookup(int lat, int model, int storage, int64_t cells) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(tune_key(lat, model, storage, size_class(cells)));
+    return it == g_tune.end() ? kBlock : it->second;
+}
+
+// Adopt the current table; a changed block size invalidates captured graphs.
+void apply_tuning(lbm_solver* s) {
+    const uint64_t ver = g_tune_version.load();
+    if (s->tune_version == ver) return;
+    const int b = tune_lookup(s->lat, s->p.model, s->p.storage, s->ncells);
+    if (b != s->block) {
+        for (int k = 0; k < 2; ++k)
+            if (s->graph[k]) {
+                cudaGraphExecDestroy(s->graph[k]);
+                s->graph[k] = nullptr;
+            }
+        s->block = b;
+    }
+    s->tune_version = ver;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_tuning_set(lbm_lattice lat, int32_t model, int32_t storage, int32_t size_class_,
+                          int32_t block) {
+    if (lattice_q(lat) == 0) return fail(LBM_EINVAL, "unknown lattice %d", (int)lat);
+    if (model != LBM_MODEL_PR && model != LBM_MODEL_IR) return fail(LBM_EINVAL, "unknown model %d", model);
+    if (storage_bytes(storage) == 0) return fail(LBM_EINVAL, "unknown storage %d", storage);
+    if (size_class_ < 0 || size_class_ > 62) return fail(LBM_EINVAL, "size class must be in 0..62");
+    if (block != 128 && block != 256 && block != 512) return fail(LBM_EINVAL, "block must be 128, 256 or 512");
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune[tune_key(lat, model, storage, size_class_)] = block;
+    }
+    g_tune_version.fetch_add(1);
+    return LBM_OK;
+}
+
+lbm_status lbm_tuning_get(lbm_lattice lat, int32_t model, int32_t storage, int64_t cells,
+                          int32_t* block, int32_t* size_class_) {
+    if (lattice_q(lat) == 0 || cells < 1) return fail(LBM_EINVAL, "bad lattice or cell count");
+    if (block) *block = tune_lookup(lat, model, storage, cells);
+    if (size_class_) *size_class_ = size_class(cells);
+    return LBM_OK;
+}
+
+lbm_status lbm_tuning_clear(void) {
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune.clear();
+    }
+    g_tune_version.fetch_add(1);
+    return LBM_OK;
+}
+
 lbm_status lbm_step(lbm_solver* s, int64_t nsteps) {
     lbm_status v = enter(s);
     if (v != LBM_OK) return v;
     if (nsteps < 0) return fail(LBM_EINVAL, "nsteps must be >= 0");
+    apply_tuning(s);
     const int64_t k = s->p.check_every;
     int64_t left = nsteps;
     while (left > 0) {

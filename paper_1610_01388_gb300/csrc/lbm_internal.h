@@ -43,6 +43,7 @@ struct StepArgs {
     double* partials;    // check step: [gridDim][kNumStats]
     uint32_t* rng_ctr;   // 16-bit storage: launch counters for stochastic rounding [2]
     int parity;          // which of the two counters this launch reads
+    int block;           // threads per block of plain steps (128, 256 or 512)
 };
 
 enum ReduceMode { kReduceFlow = 0, kReduceTotals = 1 };

@@ -39,7 +39,8 @@ EXPORTED = ["lbm_params_default", "lbm_lattice_info", "lbm_workspace_bytes", "lb
             "lbm_batch_create", "lbm_batch_add", "lbm_batch_remove", "lbm_batch_step",
             "lbm_batch_domain_status", "lbm_batch_solver", "lbm_batch_usage", "lbm_batch_destroy",
             "lbm_server_create", "lbm_server_submit", "lbm_server_advance", "lbm_server_result",
-            "lbm_server_fields", "lbm_server_pending", "lbm_server_now", "lbm_server_destroy"]
+            "lbm_server_fields", "lbm_server_pending", "lbm_server_now", "lbm_server_destroy",
+            "lbm_tuning_set", "lbm_tuning_get", "lbm_tuning_clear"]
 LBM_REQ_QUEUED, LBM_REQ_RUNNING, LBM_REQ_CONVERGED, LBM_REQ_CAPPED, LBM_REQ_FAILED = range(5)
 
 
@@ -136,6 +137,9 @@ def library():
             "lbm_server_fields": [vp, i64, vp, vp, vp, vp],
             "lbm_server_pending": [vp, P(i64), P(i64), P(sz)],
             "lbm_server_now": [vp, P(d)],
+            "lbm_tuning_set": [i32, i32, i32, i32, i32],
+            "lbm_tuning_get": [i32, i32, i32, i64, P(i32), P(i32)],
+            "lbm_tuning_clear": [],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
@@ -306,6 +310,31 @@ def lbm_get_tau(h):
 def lbm_destroy(h):
     if h:
         library().lbm_destroy(h)
+
+
+def _mdl(x):
+    return MODELS[x] if isinstance(x, str) else int(x)
+
+
+def _sto(x):
+    return STORAGES[x] if isinstance(x, str) else int(x)
+
+
+def lbm_tuning_set(lat, model, storage, size_class, block):
+    _check(library().lbm_tuning_set(_lat(lat), _mdl(model), _sto(storage), int(size_class),
+                                    int(block)))
+
+
+def lbm_tuning_get(lat, model, storage, cells):
+    """(block, size class) the library uses for a problem of `cells` cells."""
+    b, c = ctypes.c_int32(), ctypes.c_int32()
+    _check(library().lbm_tuning_get(_lat(lat), _mdl(model), _sto(storage), int(cells),
+                                    ctypes.byref(b), ctypes.byref(c)))
+    return b.value, c.value
+
+
+def lbm_tuning_clear():
+    _check(library().lbm_tuning_clear())
 
 
 # --- convenience wrapper ----------------------------------------------------

@@ -124,6 +124,22 @@ def test_workspace_bytes_cover_the_layout():
     assert lbm.lbm_workspace_bytes("D3Q27", 256, 128, 128, p64) >= 2 * 27 * 8 * cells
 
 
+def test_tuning_table_host_logic():
+    lbm.lbm_tuning_clear()
+    assert lbm.lbm_tuning_get("D3Q27", "IR", "F32", 4_194_304) == (256, 22)
+    assert lbm.lbm_tuning_get("D2Q9", "PR", "F16", 1) == (256, 0)
+    lbm.lbm_tuning_set("D3Q27", "IR", "F32", 22, 512)
+    assert lbm.lbm_tuning_get("D3Q27", "IR", "F32", 5_000_000) == (512, 22)
+    assert lbm.lbm_tuning_get("D3Q27", "PR", "F32", 5_000_000)[0] == 256   # other key
+    assert lbm.lbm_tuning_get("D3Q27", "IR", "F32", 9_000_000)[0] == 256   # other class
+    lib = lbm.library()
+    assert lib.lbm_tuning_set(3, 1, 1, 22, 300) == lbm.LBM_EINVAL
+    assert lib.lbm_tuning_set(3, 1, 9, 22, 256) == lbm.LBM_EINVAL
+    assert lib.lbm_tuning_set(9, 1, 1, 22, 256) == lbm.LBM_EINVAL
+    lbm.lbm_tuning_clear()
+    assert lbm.lbm_tuning_get("D3Q27", "IR", "F32", 5_000_000)[0] == 256
+
+
 def test_null_handle_is_rejected():
     lib = lbm.library()
     assert lib.lbm_step(None, 1) == lbm.LBM_EINVAL

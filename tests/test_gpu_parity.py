@@ -168,6 +168,32 @@ def test_graph_replay_is_bitwise_identical_to_single_launches():
     b.close()
 
 
+def test_tuned_block_sizes_agree_and_are_deterministic():
+    """Every block size of the tuning table gives the same step to round-off
+    (separately compiled kernels), and each one is bitwise reproducible."""
+    mask = W.duct_mask(40, 23, 21)
+    cells = mask.size
+    _, cls = lbm.lbm_tuning_get("D3Q19", "PR", "F32", cells)
+    pops = {}
+    try:
+        for block in (128, 256, 512):
+            lbm.lbm_tuning_set("D3Q19", "PR", "F32", cls, block)
+            runs = []
+            for _ in range(2):
+                s, _ = make_pair("D3Q19", mask, model="PR", sigma_y=1e-5, m=1e5, g=(1e-5, 0, 0))
+                s.step(150)
+                runs.append(s.get_populations())
+                s.close()
+            assert np.array_equal(runs[0], runs[1])
+            pops[block] = runs[0]
+    finally:
+        lbm.lbm_tuning_clear()
+    _, w = lbm.lbm_lattice_info("D3Q19")
+    scale = np.max(np.abs(pops[256] - w.reshape((-1, 1, 1, 1))))
+    for block in (128, 512):
+        assert np.max(np.abs(pops[block] - pops[256])) <= 1e-5 * scale
+
+
 def test_torch_workspace_matches_library_allocation():
     import torch
     mask = W.duct_mask(20, 10, 9)
