@@ -120,17 +120,28 @@ __device__ __forceinline__ uint32_t cvt_rs_bf16x2(float hi, float lo, uint32_t r
 __device__ __forceinline__ void st_u16(void* p, uint32_t v) { *reinterpret_cast<uint16_t*>(p) = (uint16_t)v; }
 
 // ---------------------------------------------------------------------------
-// storage.  R is the arithmetic type.  ld / st move the offset f_i - w_i of
-// population i between memory and registers; enc / dec convert full FP64
-// populations at the ABI (set/get populations).
+// storage.  R is the arithmetic type.  ld / st move population i between
+// memory and registers; enc / dec convert full FP64 populations at the ABI
+// (set/get populations).
 //
 // The 16-bit forms store the offset normalised by its lattice weight,
 // (f_i - w_i) / w_i, which is O(Ma) in every direction; FP16 also scales it
 // by 2^14 (exact) so offsets down to ~4e-9 stay out of FP16's subnormal range
 // while |(f_i - w_i)/w_i| up to 4 stays below its largest finite value.
 template <class S> struct Store;
+//
+// The collision works on populations in MEMORY UNITS x_i = alpha_i (f_i - w_i),
+// so loads and stores need no scaling.  Three per-direction constants carry
+// the units: beta_i = 1 / alpha_i turns x_i into an offset (moments),
+// gam_i = alpha_i w_i scales the equilibrium-type terms (which all carry a
+// factor w_i) and god_i = alpha_i 3 w_i their odd part.  For the 16-bit forms
+// alpha_i is proportional to 1 / w_i, so gam_i and god_i are the same for
+// every direction and the weights drop out of the collision arithmetic.
 template <> struct Store<float> {
     using R = float;
+    template <class L, int i> __host__ __device__ static constexpr R beta() { return 1.0f; }
+    template <class L, int i> __host__ __device__ static constexpr R gam() { return R(L::w(i)); }
+    template <class L, int i> __host__ __device__ static constexpr R god() { return L::w3f(i); }
     template <class L, int i> static __device__ __forceinline__ R ld(const float* p) { return __ldg(p); }
     static constexpr bool kStochastic = false;
     template <class L, int i> static __device__ __forceinline__ void st(float* p, R v, uint32_t) { *p = v; }
@@ -141,6 +152,9 @@ template <> struct Store<float> {
 };
 template <> struct Store<double> {
     using R = double;
+    template <class L, int i> __host__ __device__ static constexpr R beta() { return 1.0; }
+    template <class L, int i> __host__ __device__ static constexpr R gam() { return L::w(i); }
+    template <class L, int i> __host__ __device__ static constexpr R god() { return 3.0 * L::w(i); }
     template <class L, int i> static __device__ __forceinline__ R ld(const double* p) { return __ldg(p); }
     static constexpr bool kStochastic = false;
     template <class L, int i> static __device__ __forceinline__ void st(double* p, R v, uint32_t) { *p = v; }
@@ -151,23 +165,23 @@ template <> struct Store<double> {
 };
 template <> struct Store<__half> {
     using R = float;
-    static constexpr double kScale = 16384.0;   // 2^14
+    static constexpr double kScale = 16384.0;   // 2^14: alpha_i = 2^14 / w_i
+    template <class L, int i> __host__ __device__ static constexpr R beta() { return float(L::w(i) / kScale); }
+    template <class L, int i> __host__ __device__ static constexpr R gam() { return float(kScale); }
+    template <class L, int i> __host__ __device__ static constexpr R god() { return float(3.0 * kScale); }
     template <class L, int i> static __device__ __forceinline__ R ld(const __half* p) {
-        constexpr float k = float(L::w(i) / kScale);
-        return __half2float(__ldg(p)) * k;
+        return __half2float(__ldg(p));
     }
     static constexpr bool kStochastic = true;
     // stochastic rounding (unbiased: a value moves by less than half an ulp per
     // step in slowly relaxing flows, and round-to-nearest would freeze it)
     template <class L, int i> static __device__ __forceinline__ void st(__half* p, R v, uint32_t rnd) {
-        constexpr float k = float(kScale / L::w(i));
-        st_u16(p, cvt_rs_f16x2(v * k, 0.0f, rnd) >> 16);
+        st_u16(p, cvt_rs_f16x2(v, 0.0f, rnd) >> 16);
     }
     // populations i and its opposite (same weight) in one conversion
     template <class L, int i>
     static __device__ __forceinline__ void st2(__half* pi, __half* po, R vi, R vo, uint32_t rnd) {
-        constexpr float k = float(kScale / L::w(i));
-        const uint32_t d = cvt_rs_f16x2(vi * k, vo * k, rnd);
+        const uint32_t d = cvt_rs_f16x2(vi, vo, rnd);
         st_u16(pi, d >> 16);
         st_u16(po, d);
     }
@@ -175,21 +189,21 @@ template <> struct Store<__half> {
     static __device__ __forceinline__ double dec(__half v, double w) { return (double)__half2float(v) * (w / kScale); }
 };
 template <> struct Store<__nv_bfloat16> {
-    using R = float;
+    using R = float;   // alpha_i = 1 / w_i
+    template <class L, int i> __host__ __device__ static constexpr R beta() { return float(L::w(i)); }
+    template <class L, int i> __host__ __device__ static constexpr R gam() { return 1.0f; }
+    template <class L, int i> __host__ __device__ static constexpr R god() { return 3.0f; }
     template <class L, int i> static __device__ __forceinline__ R ld(const __nv_bfloat16* p) {
-        constexpr float k = float(L::w(i));
-        return __bfloat162float(__ldg(p)) * k;
+        return __bfloat162float(__ldg(p));
     }
     static constexpr bool kStochastic = true;
     template <class L, int i> static __device__ __forceinline__ void st(__nv_bfloat16* p, R v, uint32_t rnd) {
-        constexpr float k = float(1.0 / L::w(i));
-        st_u16(p, cvt_rs_bf16x2(v * k, 0.0f, rnd) >> 16);
+        st_u16(p, cvt_rs_bf16x2(v, 0.0f, rnd) >> 16);
     }
     template <class L, int i>
     static __device__ __forceinline__ void st2(__nv_bfloat16* pi, __nv_bfloat16* po, R vi, R vo,
                                                uint32_t rnd) {
-        constexpr float k = float(1.0 / L::w(i));
-        const uint32_t d = cvt_rs_bf16x2(vi * k, vo * k, rnd);
+        const uint32_t d = cvt_rs_bf16x2(vi, vo, rnd);
         st_u16(pi, d >> 16);
         st_u16(po, d);
     }
@@ -302,8 +316,9 @@ template <class R> struct Mom {
 // Grouped sums: populations are added once per velocity class (c_x = +1, -1,
 // 0; c_y = +-1; c_z = +-1; sign of c_x c_y, c_x c_z, c_y c_z) and the moments
 // are sums and differences of those class sums.  Accumulators start at -0.0,
-// the additive identity the compiler may drop.
-template <class L, class R>
+// the additive identity the compiler may drop.  f is in memory units; beta_i
+// turns each value into an offset (a multiply-add, or a plain add for beta 1).
+template <class L, class S, class R = typename Store<S>::R>
 __device__ __forceinline__ Mom<R> moments(const R (&f)[L::Q]) {
     const R z0 = R(-0.0);
     R xp = z0, xm = z0, x0 = z0, yp = z0, ym = z0, zp = z0, zm = z0;
@@ -311,7 +326,7 @@ __device__ __forceinline__ Mom<R> moments(const R (&f)[L::Q]) {
     static_for<0, L::Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
         constexpr int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
-        const R v = f[i];
+        const R v = f[i] * Store<S>::template beta<L, i>();
         if constexpr (cx == 1) xp += v;
         else if constexpr (cx == -1) xm += v;
         else x0 += v;
@@ -387,11 +402,11 @@ __device__ __forceinline__ R ctc(const Tens<R>& T, R t2xy, R t2xz, R t2yz) {
 }
 
 // ---------------------------------------------------------------------------
-// IR collision (Secs. 2.3, 3.2).  f: offsets in, offsets out.
-template <class L, class R>
+// IR collision (Secs. 2.3, 3.2).  f: memory units in, memory units out.
+template <class L, class S, class R = typename Store<S>::R>
 __device__ __forceinline__ void collide_ir(const Coef<R>& c, uint32_t flags, R (&f)[L::Q],
                                            R& drho, R (&ur)[3]) {
-    const Mom<R> m = moments<L, R>(f);
+    const Mom<R> m = moments<L, S>(f);
     const R rho = R(1) + m.d;
     const R inv = R(1) / rho;
     const R Fx = rho * c.g[0], Fy = rho * c.g[1], Fz = (L::D == 3) ? rho * c.g[2] : R(0);
@@ -420,20 +435,20 @@ __device__ __forceinline__ void collide_ir(const Coef<R>& c, uint32_t flags, R (
     const R t2xy = R(2) * T.xy, t2xz = R(2) * T.xz, t2yz = R(2) * T.yz;
     // odd part: w_i (3 rho c.u + 3/2 c.F) = 3 w_i c.(j + F), since rho u = j + F/2
     const R qx = m.jx + Fx, qy = m.jy + Fy, qz = m.jz + Fz;
-    f[0] = R(L::w(0)) * (base + R(4.5) * h0);
+    f[0] = Store<S>::template gam<L, 0>() * (base + R(4.5) * h0);
     static_for<0, (L::Q - 1) / 2>([&](auto P) {
         constexpr int i = 2 * decltype(P)::value + 1;
         constexpr int o = i + 1;
         constexpr int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
         constexpr int c2 = cx * cx + cy * cy + cz * cz;
-        const R w = R(L::w(i));
+        const R w = Store<S>::template gam<L, i>();   // w_i in memory units
         // even part e = w (base + 4.5 rho cu^2 + 4.5 h) = A + B cu^2 + C cTc (per class A, B, C)
         const R A = w * (base + R(4.5) * (h0 + k2 * R(c2)));
         const R B = w * r45;
         const R C = w * k145;
         const R cu = cdot<cx, cy, cz>(ux, uy, uz);
         const R e = A + B * (cu * cu) + C * ctc<cx, cy, cz>(T, t2xy, t2xz, t2yz);
-        const R od = odd_w<L, R>(i) * cdot<cx, cy, cz>(qx, qy, qz);
+        const R od = Store<S>::template god<L, i>() * cdot<cx, cy, cz>(qx, qy, qz);
         f[i] = e + od;
         f[o] = e - od;
     });
@@ -445,11 +460,12 @@ __device__ __forceinline__ void collide_ir(const Coef<R>& c, uint32_t flags, R (
 
 // ---------------------------------------------------------------------------
 // PR collision (Sec. 3.1 + TRT + EDM).  tau: previous step's relaxation time
-// in, this step's out.
-template <class L, class R>
+// in, this step's out.  f: memory units in, memory units out (the TRT update is
+// linear and opposite populations share their unit).
+template <class L, class S, class R = typename Store<S>::R>
 __device__ __forceinline__ void collide_pr(const Coef<R>& c, uint32_t flags, R (&f)[L::Q], R& tau,
                                            R& drho, R (&ur)[3]) {
-    const Mom<R> m = moments<L, R>(f);
+    const Mom<R> m = moments<L, S>(f);
     const R rho = R(1) + m.d;
     const R inv = R(1) / rho;
     const R ux = m.jx * inv, uy = m.jy * inv, uz = (L::D == 3) ? m.jz * inv : R(0);
@@ -480,15 +496,15 @@ __device__ __forceinline__ void collide_pr(const Coef<R>& c, uint32_t flags, R (
     const R fbase = R(-1.5) * rho * (R(2) * ug + gg);      // even part of the EDM difference
     const R r45 = R(4.5) * rho;
     {
-        const R w0 = R(L::w(0));
+        const R w0 = Store<S>::template gam<L, 0>();
         f[0] = f[0] - wp * (f[0] - w0 * base) + w0 * fbase;
     }
     static_for<0, (L::Q - 1) / 2>([&](auto P) {
         constexpr int i = 2 * decltype(P)::value + 1;
         constexpr int o = i + 1;
         constexpr int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
-        const R w = R(L::w(i));
-        const R w3 = odd_w<L, R>(i);
+        const R w = Store<S>::template gam<L, i>();    // w_i and 3 w_i in memory units
+        const R w3 = Store<S>::template god<L, i>();
         const R cu = cdot<cx, cy, cz>(ux, uy, uz);
         const R cg = cdot<cx, cy, cz>(gx, gy, gz);
         const R fe = R(0.5) * (f[i] + f[o]);
@@ -570,10 +586,10 @@ __device__ __forceinline__ void cell_step(const KParams& kp, const Coef<typename
     R drho, ur[3];
     if constexpr (MODEL == LBM_MODEL_PR) {
         R t = tau[idx];
-        collide_pr<L, R>(c, kp.flags, f, t, drho, ur);
+        collide_pr<L, S>(c, kp.flags, f, t, drho, ur);
         tau[idx] = t;
     } else {
-        collide_ir<L, R>(c, kp.flags, f, drho, ur);
+        collide_ir<L, S>(c, kp.flags, f, drho, ur);
     }
     // rest population, then opposite pairs (i, i + 1), one random word each
     Store<S>::template st<L, 0>(dst.template at<0>(idx), f[0], rnd);
@@ -712,7 +728,7 @@ k_fields(const KArgs a, const SrcPlanes<S> f, const uint32_t* __restrict__ links
     if (!(lk & kSolidBit)) {
         R v[L::Q];
         gather<L, S>(kp, f, lk, idx, v);
-        const Mom<R> m = moments<L, R>(v);
+        const Mom<R> m = moments<L, S>(v);
         const Coef<R>& c = coef<R>(a);
         const R rr = R(1) + m.d;
         const R inv = R(1) / rr;
@@ -750,7 +766,7 @@ k_reduce(const KArgs a, const SrcPlanes<S> f, const uint32_t* __restrict__ links
                 v[i] = Store<S>::template ld<L, i>(f.p[i] + idx);
             });
         }
-        const Mom<R> m = moments<L, R>(v);
+        const Mom<R> m = moments<L, S>(v);
         if constexpr (MODE == kReduceFlow) {
             const Coef<R>& c = coef<R>(a);
             const R rr = R(1) + m.d;
