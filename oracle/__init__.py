@@ -46,6 +46,7 @@ class OrcParams(ctypes.Structure):
         ("g", ctypes.c_double * 3),
         ("magic", ctypes.c_double),
         ("burnett_x", ctypes.c_int),
+        ("newton", ctypes.c_int),
     ]
 
 
@@ -96,11 +97,12 @@ def _lat(lattice):
 
 
 def params(model="IR", nu_p=0.1, sigma_y=0.0, m=0.0, gdot_c=1e-8, g=(0.0, 0.0, 0.0),
-           magic=0.25, burnett_x=False) -> OrcParams:
+           magic=0.25, burnett_x=False, newton=0) -> OrcParams:
     p = OrcParams()
     p.model = MODELS[model] if isinstance(model, str) else int(model)
     p.nu_p, p.sigma_y, p.m, p.gdot_c, p.magic = nu_p, sigma_y, m, gdot_c, magic
     p.burnett_x = 1 if burnett_x else 0
+    p.newton = int(newton)
     gg = list(g) + [0.0] * (3 - len(g))
     p.g = (ctypes.c_double * 3)(*gg)
     return p

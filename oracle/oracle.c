@@ -43,7 +43,12 @@
  *   R8  PR collision uses the tau computed in this step from the previous
  *       step's tau (explicit update of Sec. 3);
  *   R9  macroscopic fields are the moments of the streamed (pre-collision)
- *       populations, u_real = (j + F/2) / rho for both models (Sec. 2.4).
+ *       populations, u_real = (j + F/2) / rho for both models (Sec. 2.4);
+ *   R10 implicit PR (Sec. 3 names Newton iterations, no more): the unknown is
+ *       the strain rate gdot; a fixed number of iterations starts from the
+ *       explicit estimate; each iterate is clamped at gdot >= 0 and the
+ *       derivative of H is floored at 1/2 (the constant part of tau), which
+ *       only matters where the cut-off interpolation makes H non-monotone.
  *
  * Populations are full f (not offsets), layout f[i * N + cell],
  * cell = x + nx * (y + ny * z), in this file's own velocity order
@@ -73,6 +78,8 @@ typedef struct {
     double magic;     /* TRT magic number Lambda (PR) */
     int burnett_x;    /* 1: Burnett-suppressed variant for flow along x (Secs. 4.2.1,
                          4.2.2): d_xx = 0 in the PR strain rate, T_xx = 0 in IR */
+    int newton;       /* PR: Newton iterations making tau consistent with the strain
+                         rate it implies (implicit update of Sec. 3); 0 = explicit */
 } orc_params;
 
 typedef struct {
@@ -197,6 +204,39 @@ double orc_pr_nu_app(const orc_params *p, double gdot, double rho)
     return nu_app_pr(p, gdot, rho);
 }
 
+/* d nu_app / d gdot of nu_app_pr: the derivative of eq. (Pap_reg_1) above
+ * the cut-off, the slope of the linear interpolation (reading R1) below it. */
+static double nu_app_pr_slope(const orc_params *p, double gdot, double rho)
+{
+    if (gdot >= p->gdot_c) {
+        double e = exp(-p->m * gdot);
+        return p->sigma_y / rho * (p->m * e / gdot - (1.0 - e) / (gdot * gdot));
+    }
+    double nu0 = p->nu_p + p->m * p->sigma_y / rho;
+    return (nu_app_pap(p, p->gdot_c, rho) - nu0) / p->gdot_c;
+}
+
+/* Implicit PR update (Sec. 3, second approach; reading R10).  The strain
+ * rate of eq. (LBM_strain_rate) with the unknown tau is gdot(tau) = a / tau,
+ * a = sqrt(2 T:T) / (2 c_s^2); tau itself follows from gdot through eqs.
+ * (Pap_reg_1), (PR_interpolation) and (tau_visc).  Consistency is the root
+ * of H(gdot) = gdot tau(gdot) - a.  Newton iterations on H start from the
+ * explicit estimate gdot0 (previous step's tau). */
+static double pr_newton_gdot(const orc_params *p, double a, double gdot0, double rho)
+{
+    double gdot = gdot0;
+    for (int k = 0; k < p->newton; ++k) {
+        double tau = nu_app_pr(p, gdot, rho) / CS2 + 0.5;
+        double dtau = nu_app_pr_slope(p, gdot, rho) / CS2;
+        double H = gdot * tau - a;
+        double dH = tau + gdot * dtau;
+        if (dH < 0.5) dH = 0.5;
+        gdot = gdot - H / dH;
+        if (gdot < 0.0) gdot = 0.0;
+    }
+    return gdot;
+}
+
 /* diag layout (optional output of orc_collide):
  *   [0] rho, [1..3] u (velocity used in f_eq), [4..12] T, [13..21] s,
  *   [22..30] sigma, [31..39] A, [40] gdot (PR), [41] nu_app (PR),
@@ -249,6 +289,12 @@ static void collide(const orc_lattice *L, const orc_params *p, const double *fin
                 dd += D[a][b] * D[a][b];
             }
         gdot = sqrt(2.0 * dd);                 /* eq. (strainInvariant) */
+        if (p->newton > 0) {
+            double tt = 0.0;
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) tt += T[a][b] * T[a][b];
+            gdot = pr_newton_gdot(p, sqrt(2.0 * tt) / (2.0 * CS2), gdot, rho);
+        }
         nu = nu_app_pr(p, gdot, rho);          /* eqs. (Pap_reg_1), (PR_interpolation) */
         tnew = nu / CS2 + 0.5;                 /* eq. (tau_visc) */
         double todd = 0.5 + p->magic / (tnew - 0.5); /* Lambda = (1/2 - tau_odd)(1/2 - tau_even) */

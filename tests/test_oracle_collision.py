@@ -308,3 +308,83 @@ def test_burnett_suppressed_variant_drops_xx(lat):
     ir_on = oracle.params(model="IR", nu_p=0.1, sigma_y=1e-9, burnett_x=True)
     d = oracle.collide(lat, ir_on, f)[2]
     assert d["T"][0, 0] == 0.0 and d["sigma"][0, 0] == 0.0
+
+
+def _ce_state(lat, D_target, tau, rho=1.0):
+    """Chapman-Enskog population with strain rate D_target at relaxation time
+    tau: sum c c f^(1) = -2 tau rho c_s^2 D (see the strain-rate pin above)."""
+    c, w, _ = oracle.lattice_info(lat)
+    cf = c.astype(np.float64)
+    h = np.einsum("ia,ib,ab->i", cf, cf, D_target) - np.trace(D_target) / 3.0
+    return oracle.feq(lat, rho, [0, 0, 0]) - tau * rho * w * h / (1.0 / 3.0)
+
+
+def _shear(gdot):
+    """Simple shear D_xy = D_yx with sqrt(2 D:D) = gdot."""
+    Dm = np.zeros((3, 3))
+    Dm[0, 1] = Dm[1, 0] = gdot / 2.0
+    return Dm
+
+
+@pytest.mark.parametrize("lat", ["D2Q9", "D3Q19"])
+@pytest.mark.parametrize("m,sy,gdot", [
+    (1e4, 1e-5, 3e-3),     # yielded, m gdot = 30
+    (1e6, 1e-6, 2e-6),     # transition, m gdot = 2
+    (1e8, 1e-5, 1e-3),     # strongly regularised, stiff in tau
+    (1e6, 1e-6, 5e-9),     # below the cut-off gdot_C = 1e-8 (linear branch)
+])
+def test_pr_newton_recovers_consistent_tau(lat, m, sy, gdot):
+    """Sec. 3, implicit update: for a Chapman-Enskog state built with strain
+    rate gdot at tau* = 1/2 + nu_app(gdot)/c_s^2 (eqs. Pap_reg_1, tau_visc), the
+    consistent relaxation time is tau* itself.  Newton iterations from a tau_old
+    that is far off must return it, and converge quadratically: the error
+    after k + 1 iterations is far below the one after k.  The explicit update
+    (0 iterations) returns the viscosity of the lagged strain rate instead."""
+    nu, rho = 0.1, 1.0
+    p0 = oracle.params(model="PR", nu_p=nu, sigma_y=sy, m=m)
+    tstar = 0.5 + 3.0 * oracle.pr_nu_app(p0, gdot, rho)
+    f = _ce_state(lat, _shear(gdot), tstar, rho)
+    errs = []
+    for k in range(0, 40):
+        p = oracle.params(model="PR", nu_p=nu, sigma_y=sy, m=m, newton=k)
+        _, tn, d = oracle.collide(lat, p, f, tau_old=0.5 + 0.5 * (tstar - 0.5))
+        errs.append(abs(tn - tstar) / tstar)
+    assert errs[0] > 1e-3                      # lagged tau is off
+    assert errs[-1] < 1e-11
+    assert abs(d["gdot"] - gdot) < 1e-9 * gdot
+    k = next(i for i, e in enumerate(errs) if e < 1e-4)
+    assert k < 30
+    assert errs[k + 1] < 10 * errs[k] ** 1.5 + 1e-14     # superlinear once close
+
+
+@pytest.mark.parametrize("rho", [1.0, 1.05])
+def test_pr_newton_bingham_closed_form(rho):
+    """For m gdot >> 1, nu_app = nu_p + sigma_y / (rho gdot) (eq. muApparent), so
+    the consistency tau = 1/2 + 3 nu_app(a / tau) with a = tau gdot (the
+    tau-independent product given by T) is linear in tau:
+    tau = (1/2 + 3 nu_p) / (1 - 3 sigma_y / (rho a)).  Eq. (LBM_strain_rate) as
+    printed has no rho (reading R7), so the state built with rho and strain
+    rate gd carries a = rho tau gd."""
+    lat = "D3Q27"
+    nu, sy, m = 0.1, 2e-6, 1e12
+    for tau_ce, gd in ((0.8, 4e-5), (1.7, 1e-4)):
+        f = _ce_state(lat, _shear(gd), tau_ce, rho)
+        a = rho * tau_ce * gd
+        exact = (0.5 + 3 * nu) / (1 - 3 * sy / (rho * a))
+        p = oracle.params(model="PR", nu_p=nu, sigma_y=sy, m=m, newton=12)
+        tn = oracle.collide(lat, p, f, tau_old=0.6)[1]
+        assert abs(tn - exact) < 1e-11 * exact
+
+
+def test_pr_newton_newtonian_in_one_iteration():
+    """sigma_y = 0: tau does not depend on the strain rate, the consistency
+    condition is linear and one Newton iteration lands on tau = 1/2 + 3 nu_p,
+    with the strain rate that tau implies."""
+    lat = "D3Q19"
+    rng = np.random.default_rng(37)
+    f = _rand_state(lat, rng)
+    p = oracle.params(model="PR", nu_p=0.07, sigma_y=0.0, m=1e6, newton=1)
+    _, tn, d = oracle.collide(lat, p, f, tau_old=2.5)
+    assert abs(tn - (0.5 + 3 * 0.07)) < 1e-15
+    g_lag = oracle.collide(lat, oracle.params(model="PR", nu_p=0.07), f, tau_old=2.5)[2]["gdot"]
+    assert abs(d["gdot"] - g_lag * 2.5 / tn) < 1e-12 * d["gdot"]

@@ -12,7 +12,8 @@
 * Papanastasiou channel flow at finite m (PR, eq. Pap_reg_1): the steady 1D
   momentum balance gives shear stress rho g |y| exactly, so
   nu_p gdot + sigma_y (1 - exp(-m gdot)) = g |y| fixes gdot(y) and
-  u(y) = integral of gdot from |y| to h.
+  u(y) = integral of gdot from |y| to h; the Newton-implicit tau update
+  (Sec. 3) has the same steady state as the explicit one.
 * Mass conservation on periodic domains with walls; momentum gain of exactly
   F per cell and step on a wall-less periodic box.
 * Newtonian square duct against the Fourier series solution; D3Q27 free of
@@ -32,8 +33,9 @@ h = H / 2.0
 YC = np.arange(1, NY) - NY / 2.0     # row j sits at distance YC from the centre line
 
 
-def _channel(model, nu, sy, g, steps, m=0.0, magic=0.25):
-    p = oracle.params(model=model, nu_p=nu, sigma_y=sy, m=m, g=(g, 0, 0), magic=magic)
+def _channel(model, nu, sy, g, steps, m=0.0, magic=0.25, newton=0):
+    p = oracle.params(model=model, nu_p=nu, sigma_y=sy, m=m, g=(g, 0, 0), magic=magic,
+                      newton=newton)
     st = oracle.State("D2Q9", p, W.channel_mask(4, NY))
     st.step(steps - 500)
     _, ua = st.fields()
@@ -115,6 +117,22 @@ def test_channel_papanastasiou_pr(m, tol):
     with np.errstate(all="ignore"):
         ex = _papanastasiou_profile(g, nu, sy, m)
     assert np.max(np.abs(u - ex)) / ex.max() < tol
+
+
+def test_channel_papanastasiou_pr_newton_implicit():
+    """Sec. 3: the explicit (lagged) and the Newton-implicit tau updates share
+    their steady states, where tau no longer changes and so satisfies the
+    consistency condition either way.  The implicit run reaches the same
+    profile as the explicit one, and the Papanastasiou solution."""
+    nu, m = 0.1, 1e4
+    prm = W.channel_params(H=H, nu_p=nu, u_newton=0.01, bn=1.0)
+    g, sy = prm["g"], prm["sigma_y"]
+    u_imp = _channel("PR", nu, sy, g, 200_000, m=m, newton=3)
+    u_exp = _channel("PR", nu, sy, g, 200_000, m=m)
+    assert np.max(np.abs(u_imp - u_exp)) < 1e-10 * u_exp.max()
+    with np.errstate(all="ignore"):
+        ex = _papanastasiou_profile(g, nu, sy, m)
+    assert np.max(np.abs(u_imp - ex)) / ex.max() < 3e-4
 
 
 @pytest.mark.parametrize("model", ["PR", "IR"])
