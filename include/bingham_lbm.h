@@ -105,6 +105,14 @@ typedef struct {
     int32_t check_every; /* every k-th step also computes the flow rate and the
                             residual (0 = never) */
     uint32_t flags;      /* LBM_FLAG_* */
+    int32_t newton_iters; /* PR: Newton iterations of the implicit relaxation-time
+                            update (Sec. 3): each cell solves for the strain rate
+                            whose apparent viscosity gives back the tau used in
+                            eq. (LBM_strain_rate), starting from the explicit
+                            estimate (previous step's tau); iterates are clamped at
+                            gdot >= 0, the derivative is floored at 1/2.
+                            0 = explicit update (default); 0..64; IR ignores it */
+    int32_t reserved;    /* must be 0 */
 } lbm_params;
 
 /* Fills *p with defaults: IR, F32, mu_p 0.1, sigma_y 0, m 0, gammadot_c 1e-8,

@@ -91,18 +91,18 @@ __device__ __forceinline__ R cdot6(R x, R y, R z, R p, R q, R r) {
 // ---------------------------------------------------------------------------
 // Random bits for stochastic rounding.  Per cell and launch one hash of
 // (cell index, launch counter) with the PCG-based hash of Jarzynski & Olano,
-// "Hash Functions for GPU Rendering" (JCGT 9(3), 2020), then xorshift32
-// steps (Marsaglia, "Xorshift RNGs", JSS 8(14), 2003) for further words.
+// "Hash Functions for GPU Rendering" (JCGT 9(3), 2020).  Population pair p
+// takes that word times a distinct odd constant (a bijection of 32-bit words,
+// so every pair's word is exactly as uniform as the hash; one multiply).
 __device__ __forceinline__ uint32_t pcg_hash(uint32_t v) {
     const uint32_t state = v * 747796405u + 2891336453u;
     const uint32_t word = ((state >> ((state >> 28u) + 4u)) ^ state) * 277803737u;
     return (word >> 22u) ^ word;
 }
-__device__ __forceinline__ uint32_t xorshift32(uint32_t x) {
-    x ^= x << 13;
-    x ^= x >> 17;
-    x ^= x << 5;
-    return x;
+template <int p>
+__device__ __forceinline__ uint32_t pair_bits(uint32_t h) {
+    constexpr uint32_t k = 0x9e3779b9u * uint32_t(2 * p + 1);   // odd
+    return h * k;
 }
 // Hardware stochastic rounding of two FP32 values to a packed 16-bit pair
 // (PTX cvt.rs, sm_100a and later): the high half holds `hi`, the low half
@@ -219,6 +219,7 @@ template <class R> struct Coef {
     R ir_a;    // 1 / (1/2 + 3 nu_p)
     R ir_b;    // 1 / (1 + 6 nu_p)
     R six_nu;  // 6 nu_p
+    int newton;  // PR: Newton iterations of the implicit tau update
 };
 
 struct KArgs {
@@ -459,10 +460,40 @@ __device__ __forceinline__ void collide_ir(const Coef<R>& c, uint32_t flags, R (
 }
 
 // ---------------------------------------------------------------------------
+// Implicit PR update (Sec. 3, Newton iterations).  With the unknown tau the
+// strain rate of eq. (LBM_strain_rate) is gdot = a / tau, a = 1.5 sqrt(2 T:T);
+// tau = 1/2 + 3 nu_app(gdot).  Consistency is the root of
+// H(gdot) = gdot tau(gdot) - a = gdot / 2 + 3 gdot nu_app(gdot) - a, whose
+// derivative is 1/2 + 3 d(gdot nu_app)/d gdot: nu_p + (sigma_y / rho) m e^(-m gdot)
+// above the cut-off, nu_0 + 2 gdot (nu_c - nu_0) / gdot_C on the linear part
+// below it.  Iterates are clamped at 0, H' floored at 1/2.
+template <class R>
+__device__ __forceinline__ R pr_newton(const Coef<R>& c, R a, R gd, R sy_rho) {
+    const R nu0 = c.nu_p + c.m * sy_rho;
+    const R nuc = c.nu_p + sy_rho * c.e_c;
+    for (int k = 0; k < c.newton; ++k) {
+        R gnu, dgnu;   // gdot nu_app(gdot) and its derivative
+        if (gd >= c.gdot_c) {
+            const R em = expm1(-c.m * gd);
+            gnu = c.nu_p * gd - sy_rho * em;
+            dgnu = c.nu_p + sy_rho * c.m * (R(1) + em);
+        } else {
+            const R s = gd * c.inv_gc;
+            gnu = gd * ((R(1) - s) * nu0 + s * nuc);
+            dgnu = nu0 + R(2) * s * (nuc - nu0);
+        }
+        const R h = R(0.5) * gd + R(3) * gnu - a;
+        const R dh = fmax(R(0.5) + R(3) * dgnu, R(0.5));
+        gd = fmax(gd - h / dh, R(0));
+    }
+    return gd;
+}
+
+// ---------------------------------------------------------------------------
 // PR collision (Sec. 3.1 + TRT + EDM).  tau: previous step's relaxation time
 // in, this step's out.  f: memory units in, memory units out (the TRT update is
 // linear and opposite populations share their unit).
-template <class L, class S, class R = typename Store<S>::R>
+template <class L, class S, bool IMPLICIT, class R = typename Store<S>::R>
 __device__ __forceinline__ void collide_pr(const Coef<R>& c, uint32_t flags, R (&f)[L::Q], R& tau,
                                            R& drho, R (&ur)[3]) {
     const Mom<R> m = moments<L, S>(f);
@@ -471,8 +502,10 @@ __device__ __forceinline__ void collide_pr(const Coef<R>& c, uint32_t flags, R (
     const R ux = m.jx * inv, uy = m.jy * inv, uz = (L::D == 3) ? m.jz * inv : R(0);
     const Tens<R> T = noneq<L, R>(m, rho, ux, uy, uz, flags);
     // D = -T / (2 tau_old c_s^2) = -1.5 T / tau_old ; gdot = sqrt(2 D:D)
-    const R gd = R(1.5) / tau * sqrt(R(2) * tnorm2<L, R>(T));
+    const R tt = sqrt(R(2) * tnorm2<L, R>(T));
+    R gd = R(1.5) / tau * tt;
     const R sy_rho = c.sigma_y * inv;
+    if constexpr (IMPLICIT) gd = pr_newton(c, R(1.5) * tt, gd, sy_rho);
     R nu;
     if (gd >= c.gdot_c) {
         nu = c.nu_p + sy_rho * (-expm1(-c.m * gd)) / gd;
@@ -568,7 +601,7 @@ __device__ __forceinline__ void block_sum_store(V (&v)[kNumStats], double* __res
 #define BLBM_IR_MINB 0
 #endif
 template <int MODEL> constexpr int step_min_blocks() {
-    return MODEL == LBM_MODEL_PR ? BLBM_PR_MINB : BLBM_IR_MINB;
+    return MODEL == LBM_MODEL_IR ? BLBM_IR_MINB : BLBM_PR_MINB;
 }
 
 // One cell of one time step: pull, collide, store; on check steps the cell's
@@ -584,9 +617,9 @@ __device__ __forceinline__ void cell_step(const KParams& kp, const Coef<typename
     R f[L::Q];
     gather<L, S>(kp, src, lk, idx, f);
     R drho, ur[3];
-    if constexpr (MODEL == LBM_MODEL_PR) {
+    if constexpr (MODEL != LBM_MODEL_IR) {
         R t = tau[idx];
-        collide_pr<L, S>(c, kp.flags, f, t, drho, ur);
+        collide_pr<L, S, MODEL == kModelPRImplicit>(c, kp.flags, f, t, drho, ur);
         tau[idx] = t;
     } else {
         collide_ir<L, S>(c, kp.flags, f, drho, ur);
@@ -595,9 +628,8 @@ __device__ __forceinline__ void cell_step(const KParams& kp, const Coef<typename
     Store<S>::template st<L, 0>(dst.template at<0>(idx), f[0], rnd);
     static_for<0, (L::Q - 1) / 2>([&](auto P) {
         constexpr int i = 2 * decltype(P)::value + 1;
-        if constexpr (Store<S>::kStochastic) rnd = xorshift32(rnd);
         Store<S>::template st2<L, i>(dst.template at<i>(idx), dst.template at<i + 1>(idx), f[i],
-                                     f[i + 1], rnd);
+                                     f[i + 1], pair_bits<decltype(P)::value + 1>(rnd));
     });
     if constexpr (CHECK) {
         const int64_t plane = kp.plane;
@@ -843,6 +875,7 @@ template <class R> inline Coef<R> make_coef(const KParams& kp) {
     c.ir_a = (R)(1.0 / (0.5 + 3.0 * nu));
     c.ir_b = (R)(1.0 / (1.0 + 6.0 * nu));
     c.six_nu = (R)(6.0 * nu);
+    c.newton = kp.newton;
     return c;
 }
 
@@ -872,15 +905,21 @@ cudaError_t launch_step_t(bool check, const KParams& kp, const StepArgs& s, cuda
     const int grid = step_grid(kp.ncells);
     const SrcPlanes<S> src = src_planes<L, S>(s.fsrc, kp.plane);
     const DstPlanes<S> dst = dst_planes<L, S>(s.fdst, kp.plane);
+    const int block = (check || MODEL == kModelPRImplicit) ? kBlock : s.block;   // implicit: untuned
     if (check) {
         k_step<L, MODEL, S, true><<<grid, kBlock, 0, st>>>(
             a, src, dst, s.links, (R*)s.tau, (R*)s.usnap, s.partials, s.rng_ctr, s.parity);
-    } else if (s.block == 128) {
-        k_step<L, MODEL, S, false, 128><<<(kp.ncells + 127) / 128, 128, 0, st>>>(
-            a, src, dst, s.links, (R*)s.tau, (R*)s.usnap, s.partials, s.rng_ctr, s.parity);
-    } else if (s.block == 512) {
-        k_step<L, MODEL, S, false, 512><<<(kp.ncells + 511) / 512, 512, 0, st>>>(
-            a, src, dst, s.links, (R*)s.tau, (R*)s.usnap, s.partials, s.rng_ctr, s.parity);
+    } else if constexpr (MODEL != kModelPRImplicit) {
+        if (block == 128) {
+            k_step<L, MODEL, S, false, 128><<<(kp.ncells + 127) / 128, 128, 0, st>>>(
+                a, src, dst, s.links, (R*)s.tau, (R*)s.usnap, s.partials, s.rng_ctr, s.parity);
+        } else if (block == 512) {
+            k_step<L, MODEL, S, false, 512><<<(kp.ncells + 511) / 512, 512, 0, st>>>(
+                a, src, dst, s.links, (R*)s.tau, (R*)s.usnap, s.partials, s.rng_ctr, s.parity);
+        } else {
+            k_step<L, MODEL, S, false><<<grid, kBlock, 0, st>>>(
+                a, src, dst, s.links, (R*)s.tau, (R*)s.usnap, s.partials, s.rng_ctr, s.parity);
+        }
     } else {
         k_step<L, MODEL, S, false><<<grid, kBlock, 0, st>>>(
             a, src, dst, s.links, (R*)s.tau, (R*)s.usnap, s.partials, s.rng_ctr, s.parity);
@@ -891,6 +930,7 @@ cudaError_t launch_step_t(bool check, const KParams& kp, const StepArgs& s, cuda
 template <class L, class S>
 cudaError_t launch_step_model(int model, bool check, const KParams& kp, const StepArgs& s,
                               cudaStream_t st) {
+    if (model == kModelPRImplicit) return launch_step_t<L, kModelPRImplicit, S>(check, kp, s, st);
     if (model == LBM_MODEL_PR) return launch_step_t<L, LBM_MODEL_PR, S>(check, kp, s, st);
     return launch_step_t<L, LBM_MODEL_IR, S>(check, kp, s, st);
 }
@@ -920,6 +960,8 @@ cudaError_t launch_batch_t(bool check, const BatchDesc* descs, const int* block_
 template <class L, class S>
 cudaError_t launch_batch_model(int model, bool check, const BatchDesc* descs, const int* block_dom,
                                int nblocks, int phase, double* partials, cudaStream_t st) {
+    if (model == kModelPRImplicit)
+        return launch_batch_t<L, kModelPRImplicit, S>(check, descs, block_dom, nblocks, phase, partials, st);
     if (model == LBM_MODEL_PR)
         return launch_batch_t<L, LBM_MODEL_PR, S>(check, descs, block_dom, nblocks, phase, partials, st);
     return launch_batch_t<L, LBM_MODEL_IR, S>(check, descs, block_dom, nblocks, phase, partials, st);

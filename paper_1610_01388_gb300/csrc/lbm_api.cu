@@ -112,6 +112,9 @@ lbm_status validate(int lat, int nx, int ny, int nz, const uint8_t* mask, const 
     if (lat == LBM_D2Q9 && p->g[2] != 0.0) return fail(LBM_EINVAL, "D2Q9 needs g[2] == 0");
     if (p->check_every < 0) return fail(LBM_EINVAL, "check_every must be >= 0");
     if (p->flags & ~LBM_FLAG_BURNETT_X) return fail(LBM_EINVAL, "unknown flags 0x%x", p->flags);
+    if (p->newton_iters < 0 || p->newton_iters > 64)
+        return fail(LBM_EINVAL, "newton_iters must be in 0..64 (got %d)", p->newton_iters);
+    if (p->reserved != 0) return fail(LBM_EINVAL, "reserved must be 0");
     if (!mask) return fail(LBM_EINVAL, "solid_mask is NULL");
     int64_t fluid = 0;
     for (int64_t i = 0; i < n; ++i) fluid += mask[i] == 0;
@@ -154,11 +157,12 @@ cudaError_t launch_step(lbm_solver* s, bool check, cudaStream_t st) {
     a.rng_ctr = (uint32_t*)(s->stats + 2 * kNumStats);
     a.parity = s->cur;
     a.block = s->block;
+    const int km = kernel_model(s->p.model, s->kp.newton);
     switch (s->lat) {
-    case LBM_D2Q9: return launch_step_D2Q9(s->p.model, s->p.storage, check, s->kp, a, st);
-    case LBM_D3Q15: return launch_step_D3Q15(s->p.model, s->p.storage, check, s->kp, a, st);
-    case LBM_D3Q19: return launch_step_D3Q19(s->p.model, s->p.storage, check, s->kp, a, st);
-    default: return launch_step_D3Q27(s->p.model, s->p.storage, check, s->kp, a, st);
+    case LBM_D2Q9: return launch_step_D2Q9(km, s->p.storage, check, s->kp, a, st);
+    case LBM_D3Q15: return launch_step_D3Q15(km, s->p.storage, check, s->kp, a, st);
+    case LBM_D3Q19: return launch_step_D3Q19(km, s->p.storage, check, s->kp, a, st);
+    default: return launch_step_D3Q27(km, s->p.storage, check, s->kp, a, st);
     }
 }
 
@@ -395,7 +399,7 @@ static lbm_status create_impl(lbm_solver** out, lbm_lattice lat, int nx, int ny,
     kp.magic = p->magic > 0.0 ? p->magic : 0.25;
     for (int d = 0; d < 3; ++d) kp.g[d] = p->g[d];
     kp.flags = p->flags;
-    kp.half_scale = 1.0;
+    kp.newton = p->model == LBM_MODEL_PR ? p->newton_iters : 0;
     kp.div_nx = FastDiv::make((uint32_t)nx);
     kp.div_ny = FastDiv::make((uint32_t)ny);
 

@@ -142,14 +142,15 @@ lbm_status rebuild(lbm_batch* b) {
     old.swap(b->groups);
     for (auto& kv : b->doms) {
         const lbm_solver* s = kv.second.s;
+        const int km = kernel_model(s->p.model, s->kp.newton);   // kernel-side model code
         Group* g = nullptr;
         for (auto& x : b->groups)
-            if (x.lat == s->lat && x.model == s->p.model && x.storage == s->p.storage) g = &x;
+            if (x.lat == s->lat && x.model == km && x.storage == s->p.storage) g = &x;
         if (!g) {
             b->groups.emplace_back();
             g = &b->groups.back();
             g->lat = s->lat;
-            g->model = s->p.model;
+            g->model = km;
             g->storage = s->p.storage;
             for (auto& o : old)     // reuse device tables of a group that persists
                 if (o.lat == g->lat && o.model == g->model && o.storage == g->storage && o.d_desc) {

@@ -14,6 +14,12 @@ namespace blbm {
 constexpr int kBlock = 256;          // threads per block of the cell kernels
 constexpr int kNumStats = 8;         // doubles per reduction partial
 constexpr uint32_t kSolidBit = 1u << 31;
+// Kernel-side model code: PR with the Newton-implicit tau update is its own
+// instantiation, so the explicit kernels carry none of its code.
+constexpr int kModelPRImplicit = 2;
+inline int kernel_model(int model, int newton) {
+    return (model == LBM_MODEL_PR && newton > 0) ? kModelPRImplicit : model;
+}
 
 // Scalars every cell kernel needs.  Rheology is given in double; each kernel
 // rounds it to its arithmetic type.
@@ -24,7 +30,7 @@ struct KParams {
     double nu_p, sigma_y, m, gdot_c, magic;
     double g[3];
     uint32_t flags;
-    double half_scale;    // reduced-precision storage: offset scale (unused for F32/F64)
+    int newton;           // PR: Newton iterations of the implicit tau update (0 = explicit)
     FastDiv div_nx, div_ny;   // idx -> (x, y, z) without integer division
 };
 

@@ -55,7 +55,8 @@ class lbm_params(ctypes.Structure):
                 ("mu_p", ctypes.c_double), ("sigma_y", ctypes.c_double),
                 ("m", ctypes.c_double), ("gammadot_c", ctypes.c_double),
                 ("g", ctypes.c_double * 3), ("magic", ctypes.c_double),
-                ("check_every", ctypes.c_int32), ("flags", ctypes.c_uint32)]
+                ("check_every", ctypes.c_int32), ("flags", ctypes.c_uint32),
+                ("newton_iters", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class lbm_info(ctypes.Structure):
@@ -349,11 +350,12 @@ class Solver:
 
     def __init__(self, lattice, mask, model="IR", storage="F32", mu_p=0.1, sigma_y=0.0, m=0.0,
                  gammadot_c=1e-8, g=(0.0, 0.0, 0.0), magic=0.25, check_every=0, flags=0,
-                 use_torch=False, stream=None):
+                 newton_iters=0, use_torch=False, stream=None):
         self.lattice = lattice
         self.params = lbm_params_default(model=model, storage=storage, mu_p=mu_p,
                                          sigma_y=sigma_y, m=m, gammadot_c=gammadot_c, g=g,
-                                         magic=magic, check_every=check_every, flags=flags)
+                                         magic=magic, check_every=check_every, flags=flags,
+                                         newton_iters=newton_iters)
         mask = np.ascontiguousarray(mask, np.uint8)
         if mask.ndim == 2:
             mask = mask[None]

@@ -64,6 +64,7 @@ def test_params_default():
     p = lbm.lbm_params_default()
     assert p.model == lbm.LBM_MODEL_IR and p.storage == lbm.LBM_F32
     assert p.mu_p == 0.1 and p.gammadot_c == 1e-8 and p.magic == 0.25 and p.check_every == 0
+    assert p.newton_iters == 0 and p.reserved == 0
 
 
 def _create_status(lat, mask, **kw):
@@ -93,6 +94,9 @@ def _create_status(lat, mask, **kw):
     ("D2Q9", np.zeros((1, 4, 4)), {"g": (0, 0, 1e-6)}, "g[2]"),
     ("D3Q19", np.zeros((2, 2, 2)), {"check_every": -1}, "check_every"),
     ("D3Q19", np.zeros((2, 2, 2)), {"flags": 0x80}, "flags"),
+    ("D3Q19", np.zeros((2, 2, 2)), {"model": "PR", "newton_iters": -1}, "newton_iters"),
+    ("D3Q19", np.zeros((2, 2, 2)), {"model": "PR", "newton_iters": 65}, "newton_iters"),
+    ("D3Q19", np.zeros((2, 2, 2)), {"reserved": 1}, "reserved"),
 ])
 def test_create_rejects_invalid_arguments(lat, mask, kw, expect):
     st, msg = _create_status(lat, mask, **kw)

@@ -38,6 +38,9 @@ def _cases():
         ("D3Q27", por, dict(model="IR", storage="F32", mu_p=0.1, sigma_y=1e-6, g=(2e-5, 0, 0))),
         ("D3Q15", W.duct_mask(9, 10, 11), dict(model="PR", storage="F32", mu_p=0.05, sigma_y=1e-5,
                                                m=1e4, g=(1e-5, 2e-6, 0))),
+        ("D3Q19", W.duct_mask(10, 16, 16), dict(model="PR", storage="F64", mu_p=0.1,
+                                                sigma_y=du["sigma_y"], m=1e6, g=(du["g"], 0, 0),
+                                                newton_iters=3)),
     ]
 
 
