@@ -149,6 +149,20 @@ lbm_status lbm_step(lbm_solver *s, int64_t nsteps);
 /* Waits for all work enqueued on the solver's stream. */
 lbm_status lbm_sync(lbm_solver *s);
 
+/* Wait limit (no counterpart in the paper; a serving safeguard).  Every call
+ * that waits for a solver's or a batch's queued work -- lbm_sync, lbm_fields,
+ * lbm_flowrate, lbm_totals, lbm_residual, lbm_set/get_populations,
+ * lbm_set/get_tau, lbm_batch_domain_status, lbm_batch_remove, and through
+ * them lbm_server_advance -- gives up after `seconds` and returns
+ * LBM_ETIMEOUT.  It writes no output then; the queued work keeps running; the
+ * handle stays usable, and a later call waits again.  lbm_server_advance
+ * returning LBM_ETIMEOUT has queued its steps but judged no request; the next
+ * advance continues from there.  Destroy calls always wait to completion.
+ * 0 (the default) = no limit.  Process-wide; finite and >= 0, else
+ * LBM_EINVAL. */
+lbm_status lbm_set_wait_limit(double seconds);
+lbm_status lbm_get_wait_limit(double *seconds);
+
 /* Copies rho and u_real of every cell to host arrays of N doubles each; any
  * pointer may be NULL.  Synchronises. */
 lbm_status lbm_fields(lbm_solver *s, double *rho, double *ux, double *uy, double *uz);

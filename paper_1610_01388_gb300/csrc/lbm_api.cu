@@ -16,10 +16,12 @@
 #include <cstdio>
 #include <cstring>
 #include <atomic>
+#include <chrono>
 #include <map>
 #include <mutex>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/bingham_lbm.h"
@@ -136,6 +138,17 @@ lbm_status cuda_fail(lbm_solver* s, cudaError_t e, const char* what) {
     do {                                                   \
         cudaError_t e_ = (expr);                           \
         if (e_ != cudaSuccess) return cuda_fail(s, e_, what); \
+    } while (0)
+
+// Bounded wait for the solver's queued work: LBM_ETIMEOUT (handle still
+// usable, nothing written) when the wait limit runs out.
+#define WAIT(s, what)                                                                       \
+    do {                                                                                    \
+        cudaError_t e_ = bounded_sync((s)->stream);                                         \
+        if (e_ == cudaErrorNotReady)                                                        \
+            return fail(LBM_ETIMEOUT, "%s: queued work still running after the %g s wait limit", \
+                        what, wait_limit());                                                \
+        if (e_ != cudaSuccess) return cuda_fail(s, e_, what);                               \
     } while (0)
 
 lbm_status enter(const lbm_solver* s) {
@@ -310,6 +323,26 @@ cudaError_t launch_fill(void* p, int64_t n, int rsize, double value, cudaStream_
     return cudaGetLastError();
 }
 
+static std::atomic<double> g_wait_limit{0.0};
+
+double wait_limit() { return g_wait_limit.load(); }
+
+cudaError_t bounded_sync(cudaStream_t st) {
+    const double limit = g_wait_limit.load();
+    if (!(limit > 0.0)) return cudaStreamSynchronize(st);
+    const auto t0 = std::chrono::steady_clock::now();
+    for (int polls = 0;; ++polls) {
+        const cudaError_t e = cudaStreamQuery(st);
+        if (e != cudaErrorNotReady) return e;
+        const std::chrono::duration<double> dt = std::chrono::steady_clock::now() - t0;
+        if (dt.count() > limit) return cudaErrorNotReady;
+        if (polls < 64)
+            std::this_thread::yield();
+        else
+            std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+}
+
 }  // namespace blbm
 
 // ===========================================================================
@@ -329,6 +362,19 @@ const char* lbm_status_string(lbm_status st) {
     case LBM_EUNSUPPORTED: return "unsupported";
     default: return "unknown status";
     }
+}
+
+lbm_status lbm_set_wait_limit(double seconds) {
+    if (!(seconds >= 0.0) || !std::isfinite(seconds))
+        return fail(LBM_EINVAL, "wait limit must be finite and >= 0 (got %g)", seconds);
+    g_wait_limit.store(seconds);
+    return LBM_OK;
+}
+
+lbm_status lbm_get_wait_limit(double* seconds) {
+    if (!seconds) return fail(LBM_EINVAL, "seconds is NULL");
+    *seconds = g_wait_limit.load();
+    return LBM_OK;
 }
 
 lbm_status lbm_params_default(lbm_params* p) {
@@ -599,7 +645,7 @@ lbm_status lbm_step(lbm_solver* s, int64_t nsteps) {
 lbm_status lbm_sync(lbm_solver* s) {
     lbm_status v = enter(s);
     if (v != LBM_OK) return v;
-    CK(s, cudaStreamSynchronize(s->stream), "cudaStreamSynchronize");
+    WAIT(s, "lbm_sync");
     return LBM_OK;
 }
 
@@ -614,6 +660,7 @@ lbm_status lbm_fields(lbm_solver* s, double* rho, double* ux, double* uy, double
     lbm_status v = enter(s);
     if (v != LBM_OK) return v;
     if ((v = ensure_scratch(s)) != LBM_OK) return v;
+    WAIT(s, "lbm_fields");
     const size_t n = (size_t)s->ncells;
     double* d[4] = {s->scratch, s->scratch + n, s->scratch + 2 * n, s->scratch + 3 * n};
     CK(s, launch_fields(s, d[0], d[1], d[2], d[3]), "fields kernel");
@@ -625,6 +672,7 @@ lbm_status lbm_fields(lbm_solver* s, double* rho, double* ux, double* uy, double
 }
 
 static lbm_status reduce_to_host(lbm_solver* s, int mode, double* out) {
+    WAIT(s, "reduction");
     const int nb = reduce_grid(s->ncells);
     CK(s, launch_reduce(s, mode, nb), "reduction kernel");
     CK(s, launch_finalize(s->partials, nb, s->stats + kNumStats, s->stream), "finalize kernel");
@@ -661,7 +709,7 @@ lbm_status lbm_totals(lbm_solver* s, double* mass, double momentum[3]) {
 lbm_status lbm_residual(lbm_solver* s, double* residual, int64_t* at_step, double* flow_x) {
     lbm_status v = enter(s);
     if (v != LBM_OK) return v;
-    CK(s, cudaStreamSynchronize(s->stream), "residual sync");
+    WAIT(s, "lbm_residual");
     const double* r = s->host_stats;
     if (at_step) *at_step = s->last_check;
     if (flow_x) *flow_x = s->checks > 0 ? r[kStatUx] / s->nx : 0.0;
@@ -676,6 +724,7 @@ lbm_status lbm_set_populations(lbm_solver* s, const double* f) {
     if (v != LBM_OK) return v;
     if (!f) return fail(LBM_EINVAL, "f is NULL");
     if ((v = ensure_scratch(s)) != LBM_OK) return v;
+    WAIT(s, "lbm_set_populations");
     for (int q = 0; q < s->Q; ++q) {
         CK(s, cudaMemcpyAsync(s->scratch, f + (size_t)q * s->ncells, (size_t)s->ncells * sizeof(double), cudaMemcpyHostToDevice, s->stream), "population upload");
         CK(s, launch_convert(s, true, q, s->scratch), "population convert");
@@ -689,6 +738,7 @@ lbm_status lbm_get_populations(lbm_solver* s, double* f) {
     if (v != LBM_OK) return v;
     if (!f) return fail(LBM_EINVAL, "f is NULL");
     if ((v = ensure_scratch(s)) != LBM_OK) return v;
+    WAIT(s, "lbm_get_populations");
     for (int q = 0; q < s->Q; ++q) {
         CK(s, launch_convert(s, false, q, s->scratch), "population convert");
         CK(s, cudaMemcpyAsync(f + (size_t)q * s->ncells, s->scratch, (size_t)s->ncells * sizeof(double), cudaMemcpyDeviceToHost, s->stream), "population download");
@@ -702,7 +752,7 @@ lbm_status lbm_set_tau(lbm_solver* s, const double* tau) {
     if (v != LBM_OK) return v;
     if (!s->tau) return fail(LBM_EINVAL, "the IR model has no relaxation-time field");
     if (!tau) return fail(LBM_EINVAL, "tau is NULL");
-    CK(s, cudaStreamSynchronize(s->stream), "tau sync");
+    WAIT(s, "tau transfer");
     if (arith_bytes(s->p.storage) == 8) {
         CK(s, cudaMemcpy(s->tau, tau, (size_t)s->ncells * sizeof(double), cudaMemcpyHostToDevice), "tau upload");
     } else {
@@ -718,7 +768,7 @@ lbm_status lbm_get_tau(lbm_solver* s, double* tau) {
     if (v != LBM_OK) return v;
     if (!s->tau) return fail(LBM_EINVAL, "the IR model has no relaxation-time field");
     if (!tau) return fail(LBM_EINVAL, "tau is NULL");
-    CK(s, cudaStreamSynchronize(s->stream), "tau sync");
+    WAIT(s, "tau transfer");
     if (arith_bytes(s->p.storage) == 8) {
         CK(s, cudaMemcpy(tau, s->tau, (size_t)s->ncells * sizeof(double), cudaMemcpyDeviceToHost), "tau download");
     } else {

@@ -119,6 +119,15 @@ lbm_status bfail(lbm_batch* b, cudaError_t e, const char* what) {
         if (e_ != cudaSuccess) return bfail(b, e_, what);      \
     } while (0)
 
+#define BWAIT(b, what)                                                                      \
+    do {                                                                                    \
+        cudaError_t e_ = bounded_sync((b)->stream);                                         \
+        if (e_ == cudaErrorNotReady)                                                        \
+            return fail(LBM_ETIMEOUT, "%s: queued work still running after the %g s wait limit", \
+                        what, wait_limit());                                                \
+        if (e_ != cudaSuccess) return bfail(b, e_, what);                                   \
+    } while (0)
+
 lbm_status benter(const lbm_batch* b) {
     if (!b) return fail(LBM_EINVAL, "batch is NULL");
     if (b->poisoned) return fail(LBM_ECUDA, "batch is in an error state after a CUDA failure");
@@ -340,7 +349,7 @@ lbm_status lbm_batch_remove(lbm_batch* b, int64_t id) {
     if (v != LBM_OK) return v;
     auto it = b->doms.find(id);
     if (it == b->doms.end()) return fail(LBM_EINVAL, "unknown domain %lld", (long long)id);
-    BCK(b, cudaStreamSynchronize(b->stream), "batch sync");
+    BWAIT(b, "lbm_batch_remove");
     lbm_destroy(it->second.s);
     BCK(b, cudaFreeAsync(it->second.ws, b->stream), "domain release");
     b->used -= it->second.bytes;
@@ -396,7 +405,7 @@ lbm_status lbm_batch_domain_status(lbm_batch* b, int64_t id, lbm_domain_status* 
     if (v != LBM_OK) return v;
     auto it = b->doms.find(id);
     if (it == b->doms.end() || !st) return fail(LBM_EINVAL, "unknown domain %lld", (long long)id);
-    BCK(b, cudaStreamSynchronize(b->stream), "batch sync");
+    BWAIT(b, "lbm_batch_domain_status");
     const Dom& d = it->second;
     const double* r = b->h_slots + (int64_t)d.slot * kNumStats;
     std::memset(st, 0, sizeof(*st));

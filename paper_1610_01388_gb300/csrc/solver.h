@@ -20,6 +20,12 @@ struct Layout {
 };
 
 lbm_status fail(lbm_status st, const char* fmt, ...);
+
+// Waits for the work queued on `st` for at most the process-wide limit set by
+// lbm_set_wait_limit (0 = no limit).  Returns cudaErrorNotReady when the limit
+// ran out; the queued work is untouched and keeps running.
+cudaError_t bounded_sync(cudaStream_t st);
+double wait_limit();
 int lattice_q(int lat);
 size_t storage_bytes(int storage);
 size_t arith_bytes(int storage);

@@ -40,7 +40,8 @@ EXPORTED = ["lbm_params_default", "lbm_lattice_info", "lbm_workspace_bytes", "lb
             "lbm_batch_domain_status", "lbm_batch_solver", "lbm_batch_usage", "lbm_batch_destroy",
             "lbm_server_create", "lbm_server_submit", "lbm_server_advance", "lbm_server_result",
             "lbm_server_fields", "lbm_server_pending", "lbm_server_now", "lbm_server_destroy",
-            "lbm_tuning_set", "lbm_tuning_get", "lbm_tuning_clear"]
+            "lbm_tuning_set", "lbm_tuning_get", "lbm_tuning_clear", "lbm_set_wait_limit",
+            "lbm_get_wait_limit"]
 LBM_REQ_QUEUED, LBM_REQ_RUNNING, LBM_REQ_CONVERGED, LBM_REQ_CAPPED, LBM_REQ_FAILED = range(5)
 
 
@@ -141,6 +142,8 @@ def library():
             "lbm_tuning_set": [i32, i32, i32, i32, i32],
             "lbm_tuning_get": [i32, i32, i32, i64, P(i32), P(i32)],
             "lbm_tuning_clear": [],
+            "lbm_set_wait_limit": [ctypes.c_double],
+            "lbm_get_wait_limit": [P(d)],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
@@ -336,6 +339,16 @@ def lbm_tuning_get(lat, model, storage, cells):
 
 def lbm_tuning_clear():
     _check(library().lbm_tuning_clear())
+
+
+def lbm_set_wait_limit(seconds):
+    _check(library().lbm_set_wait_limit(float(seconds)))
+
+
+def lbm_get_wait_limit() -> float:
+    v = ctypes.c_double()
+    _check(library().lbm_get_wait_limit(ctypes.byref(v)))
+    return v.value
 
 
 # --- convenience wrapper ----------------------------------------------------

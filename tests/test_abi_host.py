@@ -144,6 +144,19 @@ def test_tuning_table_host_logic():
     assert lbm.lbm_tuning_get("D3Q27", "IR", "F32", 5_000_000)[0] == 256
 
 
+def test_wait_limit_host_logic():
+    assert lbm.lbm_get_wait_limit() == 0.0
+    lbm.lbm_set_wait_limit(2.5)
+    assert lbm.lbm_get_wait_limit() == 2.5
+    lib = lbm.library()
+    for bad in (-1.0, float("nan"), float("inf")):
+        assert lib.lbm_set_wait_limit(bad) == lbm.LBM_EINVAL
+    assert lbm.lbm_get_wait_limit() == 2.5
+    assert lib.lbm_get_wait_limit(None) == lbm.LBM_EINVAL
+    lbm.lbm_set_wait_limit(0.0)
+    assert lib.lbm_status_string(lbm.LBM_ETIMEOUT) == b"timeout"
+
+
 def test_null_handle_is_rejected():
     lib = lbm.library()
     assert lib.lbm_step(None, 1) == lbm.LBM_EINVAL
