@@ -375,6 +375,22 @@ def run_serving(args, storage):
     reqs = W.serving_requests(n=args.serve_requests, rate=args.serve_rate, seed=7,
                               storage=storage, max_steps=args.serve_max_steps,
                               tolerance=args.serve_tolerance)
+    schedule = None
+    if not args.no_tune:
+        # the batch schedule, tuned on a mix drawn from the same generator
+        # (another seed), outside the timed region
+        from paper_1610_01388_gb300 import autotune
+        sample = W.serving_requests(n=48, rate=args.serve_rate, seed=8, storage=storage,
+                                    max_steps=args.serve_max_steps,
+                                    tolerance=args.serve_tolerance)
+        mix = [(r["lattice"], r["mask"], dict(model=r["model"], storage=r["storage"],
+                                              mu_p=r["mu_p"], sigma_y=r["sigma_y"], m=r["m"],
+                                              g=r["g"])) for r in sample]
+        tuned = autotune.tune_batch(mix)
+        schedule = {k: v for k, v in tuned.items() if k != "tried"}
+        schedule["us_per_step_untuned"] = round(tuned["tried"]["base"] * 1e6, 1)
+        schedule["seconds_per_step"] = round(schedule["seconds_per_step"] * 1e6, 1)
+        schedule["us_per_step"] = schedule.pop("seconds_per_step")
     srv = lbm.Server(120 * (1 << 30), check_every=100)
     t0 = srv.now()
     ids = []
@@ -410,7 +426,8 @@ def run_serving(args, storage):
             "converged": int(conv.sum()),
             "capped": int(sum(r.state == lbm.LBM_REQ_CAPPED for r in res)),
             "failed": int(sum(r.state == lbm.LBM_REQ_FAILED for r in res)),
-            "aggregate_mlups": round(upd / span / 1e6, 1), "makespan_s": round(span, 3)}
+            "aggregate_mlups": round(upd / span / 1e6, 1), "makespan_s": round(span, 3),
+            "batch_schedule": schedule}
 
 
 # --- oracle arms ------------------------------------------------------------------

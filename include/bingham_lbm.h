@@ -254,7 +254,25 @@ lbm_status lbm_tuning_set(lbm_lattice lat, int32_t model, int32_t storage, int32
 /* Block used for a problem of `cells` cells, and its size class. */
 lbm_status lbm_tuning_get(lbm_lattice lat, int32_t model, int32_t storage, int64_t cells,
                           int32_t *block, int32_t *size_class);
-lbm_status lbm_tuning_clear(void);
+lbm_status lbm_tuning_clear(void);   /* also resets the batch schedule below */
+
+/* Batch schedule (no counterpart in the paper), read by every batch (and so
+ * every server) at its next lbm_batch_step:
+ *   ctas_per_sm -- per (lattice, model, storage) group: 0 (default) launches
+ *     one 256-thread CTA per 256-cell tile; n > 0 launches a persistent grid
+ *     of min(tiles, n x SMs) CTAs that walk the tiles.  0..32.
+ *   concurrency -- 1: the captured 16-step graphs run the groups as parallel
+ *     branches (they touch disjoint memory); 0 (default): one after another.
+ * Results do not depend on either: the per-cell arithmetic and the order of
+ * every reduction are the same (check-step partials are kept per tile).
+ * The project's autotuner (paper_1610_01388_gb300.autotune.tune_batch) times
+ * the candidates on a mix of domains and sets the fastest. */
+lbm_status lbm_tuning_set_batch(lbm_lattice lat, int32_t model, int32_t storage,
+                                int32_t ctas_per_sm);
+lbm_status lbm_tuning_get_batch(lbm_lattice lat, int32_t model, int32_t storage,
+                                int32_t *ctas_per_sm);
+lbm_status lbm_tuning_set_batch_concurrency(int32_t concurrent);
+lbm_status lbm_tuning_get_batch_concurrency(int32_t *concurrent);
 
 /* ------------------------------------------------------------------------
  * Batched stepping of many resident domains (no counterpart in the paper: a

@@ -87,3 +87,55 @@ def load(cache):
         lbm.lbm_tuning_set(lat, model, storage, int(cls), int(v["block"]))
         n += 1
     return n
+
+
+# --- batch schedule -------------------------------------------------------------
+
+BATCH_CTAS = (0, 1, 2, 4, 8)
+
+
+def measure_batch(mix, steps=160, warmup=32, budget=64 << 30):
+    """Wall time (s) per step of a batch holding every domain of `mix`
+    ((lattice, mask, params) tuples), graphs captured during the warm-up; the
+    time includes the host's launch work, which is what small domains pay."""
+    import time
+    b = lbm.Batch(budget, check_every=1 << 30)
+    ids = [b.add(lat, mask, **prm) for lat, mask, prm in mix]
+    b.step(warmup)
+    b.status(ids[0])
+    t0 = time.perf_counter()
+    b.step(steps)
+    b.status(ids[0])
+    dt = (time.perf_counter() - t0) / steps
+    b.close()
+    return dt
+
+
+def tune_batch(mix, steps=160):
+    """Coordinate search over the batch schedule on `mix`: group concurrency
+    first (with one CTA per tile), then, group by group, the CTAs per SM of a
+    persistent grid.  Leaves the fastest schedule set; returns it with the
+    measured seconds per step of every candidate tried."""
+    keys = sorted({(lat, prm.get("model", "IR"), prm.get("storage", "F32")) for lat, _, prm in mix})
+    for lat, model, storage in keys:
+        lbm.lbm_tuning_set_batch(lat, model, storage, 0)
+    lbm.lbm_tuning_set_batch_concurrency(False)
+    tried = {"base": measure_batch(mix, steps)}
+    best = tried["base"]
+    lbm.lbm_tuning_set_batch_concurrency(True)
+    tried["concurrent"] = measure_batch(mix, steps)
+    concurrent = tried["concurrent"] < best
+    best = min(best, tried["concurrent"])
+    lbm.lbm_tuning_set_batch_concurrency(concurrent)
+    ctas = {}
+    for key in keys:
+        ctas[key] = 0
+        for c in BATCH_CTAS[1:]:
+            lbm.lbm_tuning_set_batch(*key, c)
+            t = measure_batch(mix, steps)
+            tried[f"{'/'.join(key)}:{c}"] = t
+            if t < best:
+                best, ctas[key] = t, c
+        lbm.lbm_tuning_set_batch(*key, ctas[key])
+    return {"concurrent": concurrent, "ctas_per_sm": {"/".join(k): v for k, v in ctas.items()},
+            "seconds_per_step": best, "tried": tried}

@@ -709,14 +709,13 @@ template <class R> __device__ __forceinline__ const Coef<R>& bcoef(const BatchDe
 template <> __device__ __forceinline__ const Coef<float>& bcoef<float>(const BatchDesc& d) { return d.cf; }
 template <> __device__ __forceinline__ const Coef<double>& bcoef<double>(const BatchDesc& d) { return d.cd; }
 
+// One batch step of one tile (kBlock consecutive cells of one domain).
 template <class L, int MODEL, class S, bool CHECK>
-__global__ void __launch_bounds__(kBlock)
-k_step_batch(const BatchDesc* __restrict__ descs, const int* __restrict__ block_dom, int phase,
-             double* __restrict__ partials) {
+__device__ __forceinline__ void batch_tile(const BatchDesc& D, int tile, int phase,
+                                           double* __restrict__ partials) {
     using R = typename Store<S>::R;
-    const BatchDesc& D = descs[block_dom[blockIdx.x]];
     const KParams& kp = D.kp;
-    const int lb = blockIdx.x - D.block_begin;
+    const int lb = tile - D.block_begin;
     const int idx = lb * kBlock + threadIdx.x;
     const int cur = phase ^ D.parity0;
     const SrcStride<S> src{(const S*)D.f[cur], (int)kp.plane};
@@ -742,7 +741,21 @@ k_step_batch(const BatchDesc* __restrict__ descs, const int* __restrict__ block_
     if (active)
         cell_step<L, MODEL, S, CHECK>(kp, bcoef<R>(D), src, dst, lk, idx, (R*)D.tau, (R*)D.usnap,
                                       rnd, acc);
-    if constexpr (CHECK) block_sum_store(acc, partials + (int64_t)blockIdx.x * kNumStats);
+    if constexpr (CHECK) block_sum_store(acc, partials + (int64_t)tile * kNumStats);
+}
+
+// Batch step: the CTAs walk the tiles of every domain of the group (tile t,
+// t + gridDim.x, ...).  With one CTA per tile this is the plain launch; with
+// fewer CTAs it is a persistent grid.  Partials are indexed by tile, so check
+// steps reduce in the same order for every grid size.
+template <class L, int MODEL, class S, bool CHECK>
+__global__ void __launch_bounds__(kBlock)
+k_step_batch(const BatchDesc* __restrict__ descs, const int* __restrict__ block_dom, int ntiles,
+             int phase, double* __restrict__ partials) {
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        batch_tile<L, MODEL, S, CHECK>(descs[block_dom[t]], t, phase, partials);
+        if constexpr (CHECK) __syncthreads();   // block_sum_store's shared rows are reused
+    }
 }
 
 // macroscopic fields of the streamed populations
@@ -949,33 +962,33 @@ cudaError_t launch_step_lat(int model, int storage, bool check, const KParams& k
 
 template <class L, int MODEL, class S>
 cudaError_t launch_batch_t(bool check, const BatchDesc* descs, const int* block_dom, int nblocks,
-                           int phase, double* partials, cudaStream_t st) {
+                           int grid, int phase, double* partials, cudaStream_t st) {
     if (check)
-        k_step_batch<L, MODEL, S, true><<<nblocks, kBlock, 0, st>>>(descs, block_dom, phase, partials);
+        k_step_batch<L, MODEL, S, true><<<grid, kBlock, 0, st>>>(descs, block_dom, nblocks, phase, partials);
     else
-        k_step_batch<L, MODEL, S, false><<<nblocks, kBlock, 0, st>>>(descs, block_dom, phase, partials);
+        k_step_batch<L, MODEL, S, false><<<grid, kBlock, 0, st>>>(descs, block_dom, nblocks, phase, partials);
     return cudaGetLastError();
 }
 
 template <class L, class S>
 cudaError_t launch_batch_model(int model, bool check, const BatchDesc* descs, const int* block_dom,
-                               int nblocks, int phase, double* partials, cudaStream_t st) {
+                               int nblocks, int grid, int phase, double* partials, cudaStream_t st) {
     if (model == kModelPRImplicit)
-        return launch_batch_t<L, kModelPRImplicit, S>(check, descs, block_dom, nblocks, phase, partials, st);
+        return launch_batch_t<L, kModelPRImplicit, S>(check, descs, block_dom, nblocks, grid, phase, partials, st);
     if (model == LBM_MODEL_PR)
-        return launch_batch_t<L, LBM_MODEL_PR, S>(check, descs, block_dom, nblocks, phase, partials, st);
-    return launch_batch_t<L, LBM_MODEL_IR, S>(check, descs, block_dom, nblocks, phase, partials, st);
+        return launch_batch_t<L, LBM_MODEL_PR, S>(check, descs, block_dom, nblocks, grid, phase, partials, st);
+    return launch_batch_t<L, LBM_MODEL_IR, S>(check, descs, block_dom, nblocks, grid, phase, partials, st);
 }
 
 template <class L>
 cudaError_t launch_batch_lat(int model, int storage, bool check, const BatchDesc* descs,
-                             const int* block_dom, int nblocks, int phase, double* partials,
-                             cudaStream_t st) {
+                             const int* block_dom, int nblocks, int grid, int phase,
+                             double* partials, cudaStream_t st) {
     switch (storage) {
-    case LBM_F32: return launch_batch_model<L, float>(model, check, descs, block_dom, nblocks, phase, partials, st);
-    case LBM_F64: return launch_batch_model<L, double>(model, check, descs, block_dom, nblocks, phase, partials, st);
-    case LBM_F16_OFS: return launch_batch_model<L, __half>(model, check, descs, block_dom, nblocks, phase, partials, st);
-    case LBM_BF16_OFS: return launch_batch_model<L, __nv_bfloat16>(model, check, descs, block_dom, nblocks, phase, partials, st);
+    case LBM_F32: return launch_batch_model<L, float>(model, check, descs, block_dom, nblocks, grid, phase, partials, st);
+    case LBM_F64: return launch_batch_model<L, double>(model, check, descs, block_dom, nblocks, grid, phase, partials, st);
+    case LBM_F16_OFS: return launch_batch_model<L, __half>(model, check, descs, block_dom, nblocks, grid, phase, partials, st);
+    case LBM_BF16_OFS: return launch_batch_model<L, __nv_bfloat16>(model, check, descs, block_dom, nblocks, grid, phase, partials, st);
     default: return cudaErrorNotSupported;
     }
 }
@@ -1088,9 +1101,9 @@ template <class L> void lattice_table(int* c, double* w) {
     }                                                                                           \
     void lattice_table_##L(int* c, double* w) { lattice_table<L>(c, w); }                       \
     cudaError_t launch_step_batch_##L(int model, int storage, bool check, const BatchDesc* descs,\
-                                      const int* block_dom, int nblocks, int phase,            \
+                                      const int* block_dom, int nblocks, int grid, int phase,  \
                                       double* partials, cudaStream_t st) {                      \
-        return launch_batch_lat<L>(model, storage, check, descs, block_dom, nblocks, phase,     \
-                                   partials, st);                                               \
+        return launch_batch_lat<L>(model, storage, check, descs, block_dom, nblocks, grid,      \
+                                   phase, partials, st);                                        \
     }                                                                                           \
     }

@@ -605,6 +605,7 @@ lbm_status lbm_tuning_clear(void) {
         g_tune.clear();
     }
     g_tune_version.fetch_add(1);
+    clear_batch_schedule();
     return LBM_OK;
 }
 

@@ -13,7 +13,9 @@
 #include <cmath>
 #include <cstring>
 #include <deque>
+#include <atomic>
 #include <map>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -51,19 +53,22 @@ __global__ void k_finalize_domains(const BatchDesc* __restrict__ descs,
 }
 
 cudaError_t launch_batch(int lat, int model, int storage, bool check, const BatchDesc* d,
-                         const int* bd, int nblocks, int phase, double* partials, cudaStream_t st) {
+                         const int* bd, int nblocks, int grid, int phase, double* partials,
+                         cudaStream_t st) {
     switch (lat) {
-    case LBM_D2Q9: return launch_step_batch_D2Q9(model, storage, check, d, bd, nblocks, phase, partials, st);
-    case LBM_D3Q15: return launch_step_batch_D3Q15(model, storage, check, d, bd, nblocks, phase, partials, st);
-    case LBM_D3Q19: return launch_step_batch_D3Q19(model, storage, check, d, bd, nblocks, phase, partials, st);
-    default: return launch_step_batch_D3Q27(model, storage, check, d, bd, nblocks, phase, partials, st);
+    case LBM_D2Q9: return launch_step_batch_D2Q9(model, storage, check, d, bd, nblocks, grid, phase, partials, st);
+    case LBM_D3Q15: return launch_step_batch_D3Q15(model, storage, check, d, bd, nblocks, grid, phase, partials, st);
+    case LBM_D3Q19: return launch_step_batch_D3Q19(model, storage, check, d, bd, nblocks, grid, phase, partials, st);
+    default: return launch_step_batch_D3Q27(model, storage, check, d, bd, nblocks, grid, phase, partials, st);
     }
 }
 
 struct Group {
-    int lat = 0, model = 0, storage = 0;
+    int lat = 0, model = 0, storage = 0;   // model: kernel-side model code
+    int user_model = 0;                    // lbm_model, the schedule key
     std::vector<int64_t> ids;
-    int nblocks = 0;
+    int nblocks = 0;                       // tiles of kBlock cells
+    int grid = 0;                          // CTAs per launch (== nblocks: one per tile)
     BatchDesc* d_desc = nullptr;
     int* d_block_dom = nullptr;
     double* d_partials = nullptr;
@@ -84,7 +89,32 @@ double now_s() {
     return duration<double>(steady_clock::now().time_since_epoch()).count();
 }
 
+// Process-wide batch schedule: CTAs per SM of each (lattice, model, storage)
+// group's launch (0 = one CTA per tile) and whether captured graphs run the
+// groups as concurrent branches.  Batches adopt a change at their next step.
+std::mutex g_sched_mu;
+std::map<int, int> g_sched_ctas;
+std::atomic<int> g_sched_concurrent{0};
+std::atomic<uint64_t> g_sched_version{1};
+
+int sched_key(int lat, int model, int storage) { return (lat * 4 + model) * 8 + storage; }
+
+int sched_ctas(int lat, int model, int storage) {
+    std::lock_guard<std::mutex> lk(g_sched_mu);
+    auto it = g_sched_ctas.find(sched_key(lat, model, storage));
+    return it == g_sched_ctas.end() ? 0 : it->second;
+}
+
 }  // namespace
+
+void blbm::clear_batch_schedule() {
+    {
+        std::lock_guard<std::mutex> lk(g_sched_mu);
+        g_sched_ctas.clear();
+    }
+    g_sched_concurrent.store(0);
+    g_sched_version.fetch_add(1);
+}
 
 struct lbm_batch {
     cudaStream_t stream = nullptr;
@@ -103,6 +133,12 @@ struct lbm_batch {
     bool dirty = true;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     bool poisoned = false;
+    int sms = 1;                          // multiprocessors of the device
+    uint64_t sched_version = 0;           // schedule the groups were built with
+    bool concurrent = false;              // graphs run groups as parallel branches
+    std::vector<cudaStream_t> branch;     // capture branches, one per group
+    std::vector<cudaEvent_t> join;
+    cudaEvent_t fork = nullptr;
 };
 
 namespace {
@@ -144,9 +180,12 @@ void drop_graphs(lbm_batch* b) {
         }
 }
 
-// (Re)build the per-group device tables after the set of domains changed.
+// (Re)build the per-group device tables after the set of domains or the
+// schedule changed.
 lbm_status rebuild(lbm_batch* b) {
     drop_graphs(b);
+    b->sched_version = g_sched_version.load();
+    b->concurrent = g_sched_concurrent.load() != 0;
     std::vector<Group> old;
     old.swap(b->groups);
     for (auto& kv : b->doms) {
@@ -160,6 +199,7 @@ lbm_status rebuild(lbm_batch* b) {
             g = &b->groups.back();
             g->lat = s->lat;
             g->model = km;
+            g->user_model = s->p.model;
             g->storage = s->p.storage;
             for (auto& o : old)     // reuse device tables of a group that persists
                 if (o.lat == g->lat && o.model == g->model && o.storage == g->storage && o.d_desc) {
@@ -205,6 +245,8 @@ lbm_status rebuild(lbm_batch* b) {
             blocks += D.nblocks;
         }
         g.nblocks = blocks;
+        const int ctas = sched_ctas(g.lat, g.user_model, g.storage);
+        g.grid = ctas > 0 ? std::min(blocks, ctas * b->sms) : blocks;
         if ((int)desc.size() > g.cap_desc) {
             if (g.d_desc) cudaFreeAsync(g.d_desc, b->stream);
             g.cap_desc = (int)desc.size() * 2;
@@ -226,19 +268,54 @@ lbm_status rebuild(lbm_batch* b) {
     return LBM_OK;
 }
 
+cudaError_t launch_group(lbm_batch* b, const Group& g, bool check, int phase, cudaStream_t st) {
+    cudaError_t e = launch_batch(g.lat, g.model, g.storage, check, g.d_desc, g.d_block_dom,
+                                 g.nblocks, g.grid, phase, g.d_partials, st);
+    if (e != cudaSuccess || !check) return e;
+    k_finalize_domains<<<(int)g.ids.size(), kBlock, 0, st>>>(g.d_desc, g.d_partials, b->d_slots);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_all(lbm_batch* b, bool check, cudaStream_t st) {
     for (auto& g : b->groups) {
         if (g.ids.empty()) continue;
-        cudaError_t e = launch_batch(g.lat, g.model, g.storage, check, g.d_desc, g.d_block_dom,
-                                     g.nblocks, b->phase, g.d_partials, st);
+        cudaError_t e = launch_group(b, g, check, b->phase, st);
         if (e != cudaSuccess) return e;
-        if (check) {
-            k_finalize_domains<<<(int)g.ids.size(), kBlock, 0, st>>>(g.d_desc, g.d_partials, b->d_slots);
-            e = cudaGetLastError();
-            if (e != cudaSuccess) return e;
-        }
     }
     return cudaSuccess;
+}
+
+// Graph body with one branch per group: the groups touch disjoint memory, so
+// their step chains need no order between them.  Every forked branch is
+// joined back into the origin stream, also after an error, so the capture
+// can always be ended.
+cudaError_t capture_branches(lbm_batch* b, int par, int active) {
+    cudaError_t e = cudaSuccess;
+    if (!b->fork) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    while (e == cudaSuccess && (int)b->branch.size() < active) {
+        cudaStream_t st = nullptr;
+        cudaEvent_t ev = nullptr;
+        e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+        if (e == cudaSuccess) b->branch.push_back(st);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) b->join.push_back(ev);
+    }
+    if (e != cudaSuccess) return e;     // nothing forked yet
+    e = cudaEventRecord(b->fork, b->cap);
+    if (e != cudaSuccess) return e;
+    int k = 0;
+    for (const auto& g : b->groups) {
+        if (g.ids.empty()) continue;
+        cudaStream_t st = b->branch[k];
+        cudaError_t eb = cudaStreamWaitEvent(st, b->fork, 0);
+        for (int t = 0; t < kGraphLen && eb == cudaSuccess; ++t)
+            eb = launch_group(b, g, false, par ^ (t & 1), st);
+        cudaError_t ej = cudaEventRecord(b->join[k], st);
+        if (ej == cudaSuccess) ej = cudaStreamWaitEvent(b->cap, b->join[k], 0);
+        if (e == cudaSuccess) e = eb != cudaSuccess ? eb : ej;
+        ++k;
+    }
+    return e;
 }
 
 cudaError_t capture(lbm_batch* b, int par) {
@@ -253,9 +330,15 @@ cudaError_t capture(lbm_batch* b, int par) {
         b->phase = saved;
         return e;
     }
-    for (int t = 0; t < kGraphLen && e == cudaSuccess; ++t) {
-        e = launch_all(b, false, b->cap);
-        b->phase ^= 1;
+    int active = 0;
+    for (const auto& g : b->groups) active += !g.ids.empty();
+    if (b->concurrent && active > 1) {
+        e = capture_branches(b, par, active);
+    } else {
+        for (int t = 0; t < kGraphLen && e == cudaSuccess; ++t) {
+            e = launch_all(b, false, b->cap);
+            b->phase ^= 1;
+        }
     }
     cudaGraph_t g = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(b->cap, &g);
@@ -292,6 +375,7 @@ lbm_status lbm_batch_create(lbm_batch** out, size_t budget, int32_t check_every,
     b->k = check_every;
     b->stream = (cudaStream_t)stream;
     cudaError_t e = cudaGetDevice(&b->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_slots, sizeof(double) * kNumStats * kMaxSlots);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_slots, sizeof(double) * kNumStats * kMaxSlots);
     if (e == cudaSuccess) e = cudaMemset(b->d_slots, 0, sizeof(double) * kNumStats * kMaxSlots);
@@ -367,6 +451,7 @@ lbm_status lbm_batch_step(lbm_batch* b, int64_t nsteps) {
         b->gstep += nsteps;
         return LBM_OK;
     }
+    if (b->sched_version != g_sched_version.load()) b->dirty = true;
     if (b->dirty && (v = rebuild(b)) != LBM_OK) return v;
     int64_t left = nsteps;
     while (left > 0) {
@@ -438,6 +523,43 @@ lbm_status lbm_batch_usage(const lbm_batch* b, size_t* bytes, int64_t* domains, 
     return LBM_OK;
 }
 
+lbm_status lbm_tuning_set_batch(lbm_lattice lat, int32_t model, int32_t storage,
+                                 int32_t ctas_per_sm) {
+    if (lattice_q(lat) == 0) return fail(LBM_EINVAL, "unknown lattice %d", lat);
+    if (model != LBM_MODEL_PR && model != LBM_MODEL_IR) return fail(LBM_EINVAL, "unknown model %d", model);
+    if (storage_bytes(storage) == 0) return fail(LBM_EINVAL, "unknown storage %d", storage);
+    if (ctas_per_sm < 0 || ctas_per_sm > 32) return fail(LBM_EINVAL, "ctas_per_sm must be in 0..32");
+    {
+        std::lock_guard<std::mutex> lk(g_sched_mu);
+        g_sched_ctas[sched_key(lat, model, storage)] = ctas_per_sm;
+    }
+    g_sched_version.fetch_add(1);
+    return LBM_OK;
+}
+
+lbm_status lbm_tuning_get_batch(lbm_lattice lat, int32_t model, int32_t storage,
+                                 int32_t* ctas_per_sm) {
+    if (!ctas_per_sm) return fail(LBM_EINVAL, "ctas_per_sm is NULL");
+    if (lattice_q(lat) == 0) return fail(LBM_EINVAL, "unknown lattice %d", lat);
+    if (model != LBM_MODEL_PR && model != LBM_MODEL_IR) return fail(LBM_EINVAL, "unknown model %d", model);
+    if (storage_bytes(storage) == 0) return fail(LBM_EINVAL, "unknown storage %d", storage);
+    *ctas_per_sm = sched_ctas(lat, model, storage);
+    return LBM_OK;
+}
+
+lbm_status lbm_tuning_set_batch_concurrency(int32_t concurrent) {
+    if (concurrent != 0 && concurrent != 1) return fail(LBM_EINVAL, "concurrent must be 0 or 1");
+    g_sched_concurrent.store(concurrent);
+    g_sched_version.fetch_add(1);
+    return LBM_OK;
+}
+
+lbm_status lbm_tuning_get_batch_concurrency(int32_t* concurrent) {
+    if (!concurrent) return fail(LBM_EINVAL, "concurrent is NULL");
+    *concurrent = g_sched_concurrent.load();
+    return LBM_OK;
+}
+
 void lbm_batch_destroy(lbm_batch* b) {
     if (!b) return;
     int dev = -1;
@@ -455,6 +577,9 @@ void lbm_batch_destroy(lbm_batch* b) {
     }
     cudaStreamSynchronize(b->stream);
     if (b->cap) cudaStreamDestroy(b->cap);
+    for (cudaStream_t st : b->branch) cudaStreamDestroy(st);
+    for (cudaEvent_t ev : b->join) cudaEventDestroy(ev);
+    if (b->fork) cudaEventDestroy(b->fork);
     if (b->d_slots) cudaFree(b->d_slots);
     if (b->h_slots) cudaFreeHost(b->h_slots);
     cudaGetLastError();

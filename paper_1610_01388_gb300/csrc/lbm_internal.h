@@ -73,7 +73,8 @@ struct BatchDesc;   // per-domain descriptor of a batched launch (kernels.cuh)
     void lattice_table_##L(int* c, double* w);                                                  \
     cudaError_t launch_step_batch_##L(int model, int storage, bool check,                       \
                                       const struct BatchDesc* descs, const int* block_dom,      \
-                                      int nblocks, int phase, double* partials, cudaStream_t st);
+                                      int nblocks, int grid, int phase, double* partials,       \
+                                      cudaStream_t st);
 
 BLBM_DECLARE_LAUNCHERS(D2Q9)
 BLBM_DECLARE_LAUNCHERS(D3Q15)

@@ -27,6 +27,7 @@ lbm_status fail(lbm_status st, const char* fmt, ...);
 cudaError_t bounded_sync(cudaStream_t st);
 double wait_limit();
 int lattice_q(int lat);
+void clear_batch_schedule();   // lbm_tuning_clear's part for batches
 size_t storage_bytes(int storage);
 size_t arith_bytes(int storage);
 

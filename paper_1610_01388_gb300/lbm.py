@@ -41,7 +41,8 @@ EXPORTED = ["lbm_params_default", "lbm_lattice_info", "lbm_workspace_bytes", "lb
             "lbm_server_create", "lbm_server_submit", "lbm_server_advance", "lbm_server_result",
             "lbm_server_fields", "lbm_server_pending", "lbm_server_now", "lbm_server_destroy",
             "lbm_tuning_set", "lbm_tuning_get", "lbm_tuning_clear", "lbm_set_wait_limit",
-            "lbm_get_wait_limit"]
+            "lbm_get_wait_limit", "lbm_tuning_set_batch", "lbm_tuning_get_batch",
+            "lbm_tuning_set_batch_concurrency", "lbm_tuning_get_batch_concurrency"]
 LBM_REQ_QUEUED, LBM_REQ_RUNNING, LBM_REQ_CONVERGED, LBM_REQ_CAPPED, LBM_REQ_FAILED = range(5)
 
 
@@ -143,6 +144,10 @@ def library():
             "lbm_tuning_get": [i32, i32, i32, i64, P(i32), P(i32)],
             "lbm_tuning_clear": [],
             "lbm_set_wait_limit": [ctypes.c_double],
+            "lbm_tuning_set_batch": [i32, i32, i32, i32],
+            "lbm_tuning_get_batch": [i32, i32, i32, P(i32)],
+            "lbm_tuning_set_batch_concurrency": [i32],
+            "lbm_tuning_get_batch_concurrency": [P(i32)],
             "lbm_get_wait_limit": [P(d)],
         }
         for name, args in sig.items():
@@ -339,6 +344,28 @@ def lbm_tuning_get(lat, model, storage, cells):
 
 def lbm_tuning_clear():
     _check(library().lbm_tuning_clear())
+
+
+def lbm_tuning_set_batch(lat, model, storage, ctas_per_sm):
+    _check(library().lbm_tuning_set_batch(_lat(lat), _mdl(model), _sto(storage),
+                                          int(ctas_per_sm)))
+
+
+def lbm_tuning_get_batch(lat, model, storage) -> int:
+    v = ctypes.c_int32()
+    _check(library().lbm_tuning_get_batch(_lat(lat), _mdl(model), _sto(storage),
+                                          ctypes.byref(v)))
+    return v.value
+
+
+def lbm_tuning_set_batch_concurrency(on):
+    _check(library().lbm_tuning_set_batch_concurrency(1 if on else 0))
+
+
+def lbm_tuning_get_batch_concurrency() -> bool:
+    v = ctypes.c_int32()
+    _check(library().lbm_tuning_get_batch_concurrency(ctypes.byref(v)))
+    return bool(v.value)
 
 
 def lbm_set_wait_limit(seconds):

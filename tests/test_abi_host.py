@@ -144,6 +144,26 @@ def test_tuning_table_host_logic():
     assert lbm.lbm_tuning_get("D3Q27", "IR", "F32", 5_000_000)[0] == 256
 
 
+def test_batch_schedule_host_logic():
+    lbm.lbm_tuning_clear()
+    assert lbm.lbm_tuning_get_batch("D3Q27", "PR", "F16") == 0
+    assert lbm.lbm_tuning_get_batch_concurrency() is False
+    lbm.lbm_tuning_set_batch("D3Q27", "PR", "F16", 4)
+    lbm.lbm_tuning_set_batch_concurrency(True)
+    assert lbm.lbm_tuning_get_batch("D3Q27", "PR", "F16") == 4
+    assert lbm.lbm_tuning_get_batch("D3Q27", "IR", "F16") == 0      # other key
+    assert lbm.lbm_tuning_get_batch_concurrency() is True
+    lib = lbm.library()
+    assert lib.lbm_tuning_set_batch(3, 0, 2, 33) == lbm.LBM_EINVAL
+    assert lib.lbm_tuning_set_batch(3, 0, 2, -1) == lbm.LBM_EINVAL
+    assert lib.lbm_tuning_set_batch(7, 0, 2, 1) == lbm.LBM_EINVAL
+    assert lib.lbm_tuning_set_batch(3, 5, 2, 1) == lbm.LBM_EINVAL
+    assert lib.lbm_tuning_set_batch_concurrency(2) == lbm.LBM_EINVAL
+    lbm.lbm_tuning_clear()
+    assert lbm.lbm_tuning_get_batch("D3Q27", "PR", "F16") == 0
+    assert lbm.lbm_tuning_get_batch_concurrency() is False
+
+
 def test_wait_limit_host_logic():
     assert lbm.lbm_get_wait_limit() == 0.0
     lbm.lbm_set_wait_limit(2.5)

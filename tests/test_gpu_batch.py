@@ -75,6 +75,36 @@ def test_mixed_batch_matches_single_domain_runs():
     b.close()
 
 
+def _run_mix(n, k=50):
+    b = lbm.Batch(4 * GB, check_every=k)
+    ids = [b.add(lat, mask, **prm) for lat, mask, prm in _cases()]
+    b.step(n)
+    out = [(lbm.lbm_get_populations(b.solver(d)), b.status(d)) for d in ids]
+    b.close()
+    return out
+
+
+@pytest.mark.parametrize("ctas,concurrent", [(1, False), (3, False), (0, True), (2, True)])
+def test_batch_schedule_does_not_change_results(ctas, concurrent):
+    """A persistent grid (ctas_per_sm > 0) and concurrent group branches in
+    the graphs change only the launch shape: populations, residuals and flow
+    rates stay bit for bit those of the default schedule."""
+    n = 333
+    lbm.lbm_tuning_clear()
+    ref = _run_mix(n)
+    try:
+        for lat, _, prm in _cases():
+            lbm.lbm_tuning_set_batch(lat, prm["model"], prm["storage"], ctas)
+        lbm.lbm_tuning_set_batch_concurrency(concurrent)
+        got = _run_mix(n)
+    finally:
+        lbm.lbm_tuning_clear()
+    for (fa, sa), (fb, sb) in zip(ref, got):
+        assert np.array_equal(fa, fb)
+        assert sa.steps == sb.steps and sa.checks == sb.checks
+        assert sa.residual == sb.residual and list(sa.flow) == list(sb.flow)
+
+
 def test_budget_and_add_remove_mid_run():
     lat, mask, prm = _cases()[2]
     need = lbm.lbm_workspace_bytes(lat, mask.shape[2], mask.shape[1], mask.shape[0],
