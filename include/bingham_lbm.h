@@ -193,6 +193,14 @@ lbm_status lbm_set_populations(lbm_solver *s, const double *f);
 lbm_status lbm_get_populations(lbm_solver *s, double *f);
 
 /* PR relaxation-time field (host, N doubles).  LBM_EINVAL for IR. */
+/* Full FP64 populations of n listed cells (host array of cell indices
+ * x + nx (y + ny z), each in 0..cells-1; n <= 2^24), in the library's velocity
+ * order: f[i * n + k] = f_i(cells[k]), a host array of Q n doubles.  A probe of
+ * a few cells of a large domain without reading the whole state back (no
+ * counterpart in the paper).  Allocates 8 (Q + 1) n bytes of device memory
+ * for the call; synchronises. */
+lbm_status lbm_get_populations_cells(lbm_solver *s, const int64_t *cells, int64_t n, double *f);
+
 lbm_status lbm_set_tau(lbm_solver *s, const double *tau);
 lbm_status lbm_get_tau(lbm_solver *s, double *tau);
 

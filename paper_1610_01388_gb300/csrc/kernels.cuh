@@ -871,6 +871,20 @@ k_convert(const KParams kp, int q, bool to_device, S* __restrict__ f, double* __
         buf[idx] = Store<S>::dec(*p, w) + w;
 }
 
+// full FP64 populations of listed cells: out[i * n + k] = f_i(cells[k])
+template <class L, class S>
+__global__ void __launch_bounds__(kBlock)
+k_gather_cells(const KParams kp, const S* __restrict__ f, const int64_t* __restrict__ cells,
+               int n, double* __restrict__ out) {
+    const int k = blockIdx.x * kBlock + threadIdx.x;
+    if (k >= n) return;
+    const int64_t c = cells[k];
+    static_for<0, L::Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        out[(int64_t)i * n + k] = Store<S>::dec(f[(int64_t)i * kp.plane + c], L::w(i)) + L::w(i);
+    });
+}
+
 // ---------------------------------------------------------------------------
 // host-side helpers for the per-lattice launchers
 template <class R> inline Coef<R> make_coef(const KParams& kp) {
@@ -1062,6 +1076,20 @@ cudaError_t launch_convert_lat(int storage, bool to_device, const KParams& kp, i
     return cudaGetLastError();
 }
 
+template <class L>
+cudaError_t launch_gather_lat(int storage, const KParams& kp, const void* f, const int64_t* cells,
+                              int n, double* out, cudaStream_t st) {
+    const int grid = (n + kBlock - 1) / kBlock;
+    switch (storage) {
+    case LBM_F32: k_gather_cells<L, float><<<grid, kBlock, 0, st>>>(kp, (const float*)f, cells, n, out); break;
+    case LBM_F64: k_gather_cells<L, double><<<grid, kBlock, 0, st>>>(kp, (const double*)f, cells, n, out); break;
+    case LBM_F16_OFS: k_gather_cells<L, __half><<<grid, kBlock, 0, st>>>(kp, (const __half*)f, cells, n, out); break;
+    case LBM_BF16_OFS: k_gather_cells<L, __nv_bfloat16><<<grid, kBlock, 0, st>>>(kp, (const __nv_bfloat16*)f, cells, n, out); break;
+    default: return cudaErrorNotSupported;
+    }
+    return cudaGetLastError();
+}
+
 template <class L> void lattice_table(int* c, double* w) {
     for (int i = 0; i < L::Q; ++i) {
         if (c) {
@@ -1100,6 +1128,10 @@ template <class L> void lattice_table(int* c, double* w) {
         return launch_convert_lat<L>(storage, to_device, kp, q, f, plane_buf, st);              \
     }                                                                                           \
     void lattice_table_##L(int* c, double* w) { lattice_table<L>(c, w); }                       \
+    cudaError_t launch_gather_##L(int storage, const KParams& kp, const void* f,               \
+                                  const int64_t* cells, int n, double* out, cudaStream_t st) {  \
+        return launch_gather_lat<L>(storage, kp, f, cells, n, out, st);                         \
+    }                                                                                           \
     cudaError_t launch_step_batch_##L(int model, int storage, bool check, const BatchDesc* descs,\
                                       const int* block_dom, int nblocks, int grid, int phase,  \
                                       double* partials, cudaStream_t st) {                      \

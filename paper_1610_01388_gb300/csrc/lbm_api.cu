@@ -748,6 +748,41 @@ lbm_status lbm_get_populations(lbm_solver* s, double* f) {
     return LBM_OK;
 }
 
+lbm_status lbm_get_populations_cells(lbm_solver* s, const int64_t* cells, int64_t n, double* f) {
+    lbm_status v = enter(s);
+    if (v != LBM_OK) return v;
+    if (n < 0 || n > (int64_t)1 << 24) return fail(LBM_EINVAL, "n must be in 0..2^24");
+    if (n == 0) return LBM_OK;
+    if (!cells || !f) return fail(LBM_EINVAL, "cells and f must be non-NULL");
+    for (int64_t k = 0; k < n; ++k)
+        if (cells[k] < 0 || cells[k] >= s->ncells)
+            return fail(LBM_EINVAL, "cells[%lld] = %lld is outside 0..%d", (long long)k,
+                        (long long)cells[k], s->ncells - 1);
+    WAIT(s, "lbm_get_populations_cells");
+    int64_t* d_cells = nullptr;
+    double* d_out = nullptr;
+    const size_t out_bytes = (size_t)n * s->Q * sizeof(double);
+    cudaError_t e = cudaMallocAsync((void**)&d_cells, (size_t)n * sizeof(int64_t), s->stream);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&d_out, out_bytes, s->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_cells, cells, (size_t)n * sizeof(int64_t), cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) {
+        const void* fcur = s->f[s->cur];
+        switch (s->lat) {
+        case LBM_D2Q9: e = launch_gather_D2Q9(s->p.storage, s->kp, fcur, d_cells, (int)n, d_out, s->stream); break;
+        case LBM_D3Q15: e = launch_gather_D3Q15(s->p.storage, s->kp, fcur, d_cells, (int)n, d_out, s->stream); break;
+        case LBM_D3Q19: e = launch_gather_D3Q19(s->p.storage, s->kp, fcur, d_cells, (int)n, d_out, s->stream); break;
+        default: e = launch_gather_D3Q27(s->p.storage, s->kp, fcur, d_cells, (int)n, d_out, s->stream); break;
+        }
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(f, d_out, out_bytes, cudaMemcpyDeviceToHost, s->stream);
+    if (d_cells) cudaFreeAsync(d_cells, s->stream);
+    if (d_out) cudaFreeAsync(d_out, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "population gather");
+    return LBM_OK;
+}
+
 lbm_status lbm_set_tau(lbm_solver* s, const double* tau) {
     lbm_status v = enter(s);
     if (v != LBM_OK) return v;

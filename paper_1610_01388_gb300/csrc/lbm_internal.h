@@ -71,6 +71,8 @@ struct BatchDesc;   // per-domain descriptor of a batched launch (kernels.cuh)
     cudaError_t launch_convert_##L(int storage, bool to_device, const KParams& kp, int q,       \
                                    void* f, double* plane_buf, cudaStream_t st);                \
     void lattice_table_##L(int* c, double* w);                                                  \
+    cudaError_t launch_gather_##L(int storage, const KParams& kp, const void* f,               \
+                                  const int64_t* cells, int n, double* out, cudaStream_t st);   \
     cudaError_t launch_step_batch_##L(int model, int storage, bool check,                       \
                                       const struct BatchDesc* descs, const int* block_dom,      \
                                       int nblocks, int grid, int phase, double* partials,       \

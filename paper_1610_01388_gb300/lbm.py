@@ -41,7 +41,7 @@ EXPORTED = ["lbm_params_default", "lbm_lattice_info", "lbm_workspace_bytes", "lb
             "lbm_server_create", "lbm_server_submit", "lbm_server_advance", "lbm_server_result",
             "lbm_server_fields", "lbm_server_pending", "lbm_server_now", "lbm_server_destroy",
             "lbm_tuning_set", "lbm_tuning_get", "lbm_tuning_clear", "lbm_set_wait_limit",
-            "lbm_get_wait_limit", "lbm_tuning_set_batch", "lbm_tuning_get_batch",
+            "lbm_get_wait_limit", "lbm_get_populations_cells", "lbm_tuning_set_batch", "lbm_tuning_get_batch",
             "lbm_tuning_set_batch_concurrency", "lbm_tuning_get_batch_concurrency"]
 LBM_REQ_QUEUED, LBM_REQ_RUNNING, LBM_REQ_CONVERGED, LBM_REQ_CAPPED, LBM_REQ_FAILED = range(5)
 
@@ -144,6 +144,7 @@ def library():
             "lbm_tuning_get": [i32, i32, i32, i64, P(i32), P(i32)],
             "lbm_tuning_clear": [],
             "lbm_set_wait_limit": [ctypes.c_double],
+            "lbm_get_populations_cells": [vp, vp, i64, vp],
             "lbm_tuning_set_batch": [i32, i32, i32, i32],
             "lbm_tuning_get_batch": [i32, i32, i32, P(i32)],
             "lbm_tuning_set_batch_concurrency": [i32],
@@ -366,6 +367,14 @@ def lbm_tuning_get_batch_concurrency() -> bool:
     v = ctypes.c_int32()
     _check(library().lbm_tuning_get_batch_concurrency(ctypes.byref(v)))
     return bool(v.value)
+
+
+def lbm_get_populations_cells(h, cells, Q):
+    """(Q, n) FP64 populations of the listed cells, library velocity order."""
+    cells = np.ascontiguousarray(cells, np.int64)
+    out = np.zeros((Q, cells.size), np.float64)
+    _check(library().lbm_get_populations_cells(h, _ptr(cells), cells.size, _ptr(out)))
+    return out
 
 
 def lbm_set_wait_limit(seconds):

@@ -56,40 +56,104 @@ def cylinder_mask(L: int = 80, D: float = 32.0, shift: float = 0.0) -> np.ndarra
 
 def porous_mask(n: int | tuple = 64, porosity: float = 0.7, r_min: float = 6.0,
                 r_max: float = 10.0, seed: int = 1, max_attempts: int = 10_000_000):
-    """Random non-overlapping spheres in a periodic box.
+    """Random non-overlapping spheres in a periodic box (random sequential
+    addition).
+
+    Candidates (centre uniform in the box, radius uniform in [r_min, r_max])
+    are drawn in chunks of 256 from numpy's PCG64 seeded with `seed` and taken
+    in order: a candidate is kept if it overlaps no sphere kept before it
+    (periodic minimum-image distance below the sum of the radii), and painted
+    into the mask (a cell is solid if its centre lies inside a sphere).  The
+    packing stops once the solid fraction reaches 1 - porosity, or at the
+    first chunk boundary after max_attempts candidates (jamming).
 
     Returns (mask, info) with info = {"porosity", "spheres", "attempts",
-    "reached"}; `reached` is False if the attempt cap stopped the packing
-    before the target porosity (jamming).  Generator: numpy PCG64 seeded
-    with `seed`.
+    "reached"}.  Overlap tests look only at the 27 neighbouring bins of edge
+    >= 2 r_max when the box holds at least 3 bins per axis, which gives the
+    same accept / reject decisions as testing every kept sphere.
     """
     nx, ny, nz = (n, n, n) if isinstance(n, int) else n
     rng = np.random.Generator(np.random.PCG64(seed))
     mask = np.zeros((nz, ny, nx), np.uint8)
     box = np.array([nx, ny, nz], np.float64)
+    total = nx * ny * nz
+    target_solid = (1.0 - porosity) * total
+    nb = np.floor(box / (2.0 * r_max)).astype(int)
+    binned = bool(np.all(nb >= 3))
+    edge = box / np.maximum(nb, 1)
+    cap = int(np.ceil((float(edge.max()) / (2.0 * r_min) + 1.0) ** 3)) + 1
+    grid = np.full((nb[0], nb[1], nb[2], cap), -1, np.int64) if binned else None
+    fill = np.zeros((nb[0], nb[1], nb[2]), np.int64) if binned else None
+    offs = np.array([(a, b, c) for a in (-1, 0, 1) for b in (-1, 0, 1) for c in (-1, 0, 1)])
     centres = np.zeros((0, 3), np.float64)
     radii = np.zeros(0, np.float64)
     solid = 0
-    total = nx * ny * nz
-    target_solid = (1.0 - porosity) * total
     attempts = 0
-    batch = 256
-    while solid < target_solid and attempts < max_attempts:
-        cand = rng.random((batch, 3)) * box
-        rad = r_min + (r_max - r_min) * rng.random(batch)
-        for k in range(batch):
-            attempts += 1
-            if len(radii):
-                d = centres - cand[k]
+    chunk, group = 256, 16
+
+    def hits_kept(cand, rad):
+        """Candidates (m, 3) overlapping a sphere kept before this group."""
+        if len(radii) == 0:
+            return np.zeros(len(rad), bool)
+        if not binned:
+            d = centres[None, :, :] - cand[:, None, :]
+            d -= box * np.round(d / box)
+            return np.any(np.sqrt(np.sum(d * d, axis=2)) < radii[None, :] + rad[:, None], axis=1)
+        b = np.minimum((cand / edge).astype(int), nb - 1)
+        nbins = (b[:, None, :] + offs[None, :, :]) % nb              # (m, 27, 3)
+        top = int(fill.max())
+        idx = grid[nbins[..., 0], nbins[..., 1], nbins[..., 2], :top].reshape(len(rad), -1)
+        valid = idx >= 0
+        j = np.where(valid, idx, 0)
+        d = centres[j] - cand[:, None, :]
+        d -= box * np.round(d / box)
+        dist = np.sqrt(np.sum(d * d, axis=2))
+        return np.any(valid & (dist < radii[j] + rad[:, None]), axis=1)
+
+    done = False
+    while not done and solid < target_solid and attempts < max_attempts:
+        cs, rs = [], []
+        for _ in range(group):
+            cs.append(rng.random((chunk, 3)) * box)
+            rs.append(r_min + (r_max - r_min) * rng.random(chunk))
+        cand, rad = np.concatenate(cs), np.concatenate(rs)
+        # chunks are taken while fewer than max_attempts candidates were drawn
+        limit = len(rad)
+        for ci in range(1, group):
+            if attempts + ci * chunk >= max_attempts:
+                limit, done = ci * chunk, True
+                break
+        rejected = hits_kept(cand[:limit], rad[:limit])
+        new_c, new_r = [], []
+        stop = None
+        for k in np.flatnonzero(~rejected):
+            if new_r:
+                d = np.asarray(new_c) - cand[k]
                 d -= box * np.round(d / box)
-                dist = np.sqrt(np.sum(d * d, axis=1))
-                if np.any(dist < radii + rad[k]):
+                if np.any(np.sqrt(np.sum(d * d, axis=1)) < np.asarray(new_r) + rad[k]):
                     continue
-            centres = np.vstack([centres, cand[k]])
-            radii = np.append(radii, rad[k])
+            new_c.append(cand[k])
+            new_r.append(rad[k])
             solid += _paint_sphere(mask, cand[k], rad[k])
             if solid >= target_solid:
+                stop = int(k)
                 break
+        if stop is not None:
+            attempts += stop + 1
+            done = True
+        else:
+            attempts += limit
+        if new_r:
+            first = len(radii)
+            centres = np.vstack([centres, np.asarray(new_c)])
+            radii = np.concatenate([radii, np.asarray(new_r)])
+            if binned:
+                for s_idx in range(first, len(radii)):
+                    bx, by, bz = np.minimum((centres[s_idx] / edge).astype(int), nb - 1)
+                    if fill[bx, by, bz] >= cap:
+                        raise RuntimeError("sphere bin overflow")
+                    grid[bx, by, bz, fill[bx, by, bz]] = s_idx
+                    fill[bx, by, bz] += 1
     info = {"porosity": 1.0 - mask.sum() / total, "spheres": int(len(radii)),
             "attempts": attempts, "reached": bool(solid >= target_solid)}
     return mask, info

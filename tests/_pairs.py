@@ -62,3 +62,42 @@ def rel_l2_u(s, o):
     a, b = ug[:, fl], uo[:, fl]
     den = np.sqrt(np.sum(b * b))
     return float(np.sqrt(np.sum((a - b) ** 2)) / den) if den > 0 else float(np.sqrt(np.sum(a * a)))
+
+
+def pulled_inputs(c, mask, cells, gather):
+    """Streamed inputs of `cells` in the library's velocity order, (n, Q):
+    f_i(x - c_i) with periodic wrap, or the cell's own f_opp(i)(x) where x - c_i
+    is solid (eq. 8 with halfway bounce-back).  gather(idx) returns the (Q, m)
+    populations of the cells idx, library order."""
+    Q = len(c)
+    opp = np.array([next(j for j in range(Q) if np.array_equal(c[j], -c[i])) for i in range(Q)])
+    nz, ny, nx = mask.shape
+    flat = mask.reshape(-1)
+    z, y, x = cells // (nx * ny), (cells // nx) % ny, cells % nx
+    nb = (((z[:, None] - c[None, :, 2]) % nz) * ny + (y[:, None] - c[None, :, 1]) % ny) * nx \
+        + (x[:, None] - c[None, :, 0]) % nx
+    probe = np.unique(np.concatenate([cells, nb.reshape(-1)]))
+    fp = gather(probe)
+    icell = np.searchsorted(probe, cells)
+    inb = np.searchsorted(probe, nb)
+    fin = np.empty((cells.size, Q))
+    for i in range(Q):
+        solid = flat[nb[:, i]] != 0
+        fin[:, i] = np.where(solid, fp[opp[i], icell], fp[i, inb[:, i]])
+    return fin
+
+
+def oracle_collide_cells(lat, p, fin, tau_old):
+    """Oracle single-cell collisions of pulled inputs (n, Q, library order);
+    returns ((Q, n) post-collision populations in library order, (n,) tau)."""
+    po = perm_gpu_to_oracle(lat)           # oracle direction of library direction k
+    n, Q = fin.shape
+    out = np.empty((Q, n))
+    tau = np.empty(n)
+    fo_in = np.empty(Q)
+    for k in range(n):
+        fo_in[po] = fin[k]
+        fo, tn, _ = oracle.collide(lat, p, fo_in, tau_old=float(tau_old[k]))
+        out[:, k] = fo[po]
+        tau[k] = tn
+    return out, tau

@@ -89,3 +89,83 @@ def test_fullsize_channel_fp64_20k_steps():
         o.step(20000)
         assert rel_l2_u(s, o) < 1e-11
         s.close()
+
+
+def _ulp16(x, storage):
+    """Spacing of the 16-bit format at |x| (FP16: 10 fraction bits, normal
+    from 2^-14; BF16: 7 fraction bits)."""
+    frac, emin = (10, -14) if storage == "F16" else (7, -126)
+    e = np.floor(np.log2(np.maximum(np.abs(x), 2.0 ** emin)))
+    return 2.0 ** (e - frac)
+
+
+def _units(f, w, storage):
+    """Populations in the stored unit: 2^14 (f - w) / w for FP16, (f - w) / w
+    for BF16 (the forms the storage documents)."""
+    return (f - w[:, None]) / w[:, None] * (16384.0 if storage == "F16" else 1.0)
+
+
+def _reduced_precision_sampled_step(lat, mask, model, storage, steps, nsample, **kw):
+    """One step of sampled cells at full size for 16-bit storage.  The GPU
+    state after `steps` steps is probed cell by cell (lbm_get_populations_cells);
+    the test streams it itself (pulled_inputs: eq. 8 with halfway bounce-back)
+    and the oracle's FP64 single-cell collision gives the post-collision
+    values.  The GPU's next stored values must be within one 16-bit spacing of
+    them (the stochastic rounding picks one of the two neighbours of its FP32
+    result), plus FP32 round-off."""
+    import oracle
+    from _pairs import oracle_collide_cells, pulled_inputs
+    # no full oracle state: at 512^3 its FP64 populations alone are 29 GB
+    s = lbm.Solver(lat, mask, model=model, storage=storage, mu_p=kw["nu_p"], sigma_y=kw["sigma_y"],
+                   m=kw["m"], g=kw["g"], check_every=100)
+    p = oracle.params(model=model, nu_p=kw["nu_p"], sigma_y=kw["sigma_y"], m=kw["m"], g=kw["g"])
+    s.step(steps)
+    c, w = lbm.lbm_lattice_info(lat)
+    cells = _sample(mask, nsample, seed=steps)
+    fin = pulled_inputs(c, mask, cells, lambda idx: lbm.lbm_get_populations_cells(s.h, idx, len(w)))
+    tau_old = s.get_tau().reshape(-1)[cells] if model == "PR" else np.zeros(cells.size)
+    want, want_tau = oracle_collide_cells(lat, p, fin, tau_old)
+    s.step(1)
+    got = lbm.lbm_get_populations_cells(s.h, cells, len(w))
+    xw, xg = _units(want, w, storage), _units(got, w, storage)
+    tol = _ulp16(np.maximum(np.abs(xw), np.abs(xg)), storage) + 1e-5 * np.max(np.abs(xw), axis=0)
+    assert np.all(np.abs(xg - xw) <= tol), (lat, model, storage, np.max(np.abs(xg - xw) / tol))
+    if model == "PR":
+        got_tau = s.get_tau().reshape(-1)[cells]
+        assert np.max(np.abs(got_tau - want_tau) / want_tau) < 1e-5
+    s.close()
+
+
+@pytest.mark.parametrize("storage", ["F16", "BF16"])
+@pytest.mark.parametrize("model", ["PR", "IR"])
+def test_fullsize_precision_duct_d3q27(storage, model):
+    """Precision workload: square duct 512 x 192 x 192 (191 x 191 fluid), D3Q27,
+    16-bit offset storage, Bn = 2, from rest."""
+    prm = W.duct_params(H=191, nu_p=0.1, u_newton=0.02, bn=2.0)
+    mask = W.duct_mask(512, 192, 192)
+    _reduced_precision_sampled_step("D3Q27", mask, model, storage, 300, 3000, nu_p=0.1,
+                                    sigma_y=prm["sigma_y"], m=1e6, g=(prm["g"], 0.0, 0.0))
+
+
+_POROUS512 = {}
+
+
+def _porous512():
+    """Precision workload's porous box: 512^3, spheres r in [6, 10], target
+    porosity 0.6, seed 1.  Random sequential addition jams above 0.6; the
+    packing stops at 2e6 candidates (porosity ~0.67, asserted below 0.7)."""
+    if "m" not in _POROUS512:
+        mask, info = W.porous_mask(512, porosity=0.6, r_min=6, r_max=10, seed=1,
+                                   max_attempts=2_000_000)
+        assert 0.6 <= info["porosity"] < 0.7
+        _POROUS512["m"] = mask
+    return _POROUS512["m"]
+
+
+@pytest.mark.parametrize("storage", ["F16", "BF16"])
+@pytest.mark.parametrize("model", ["PR", "IR"])
+def test_fullsize_precision_porous512_d3q27(storage, model):
+    """Precision workload: 512^3 porous box, D3Q27, 16-bit offset storage,
+    body-force driven from rest."""
+    _reduced_precision_sampled_step("D3Q27", _porous512(), model, storage, 200, 3000, nu_p=0.1,
+                                    sigma_y=2e-6, m=1e6, g=(2e-6, 0.0, 0.0))
