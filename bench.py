@@ -71,14 +71,14 @@ def workload_config(extra=None):
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
 # step kernels on this workload (256x128x128 duct), from one one-pass ncu
-# capture of this script.  Keyed by storage, model and block size; valid only
-# for the device-code sources they were captured with (KERNEL_FINGERPRINT),
-# reported as null once any of them changes.
+# capture of this script.  Keyed by storage, model, block size and cells per
+# thread; valid only for the device-code sources they were captured with
+# (KERNEL_FINGERPRINT), reported as null once any of them changes.
 NCU_TRAFFIC = {
-    ("F32", "IR", 128): 855843652, ("F32", "IR", 256): 855572268, ("F32", "IR", 512): 857437408,
-    ("F32", "PR", 128): 890018589, ("F32", "PR", 256): 889872329, ("F32", "PR", 512): 890397268,
-    ("F16", "IR", 128): 419228455, ("F16", "IR", 256): 418371397, ("F16", "IR", 512): 418887682,
-    ("F16", "PR", 128): 451110787, ("F16", "PR", 256): 450535906, ("F16", "PR", 512): 450572550,
+    ("F32", "IR", 128, 1): 855843652, ("F32", "IR", 256, 1): 855572268, ("F32", "IR", 512, 1): 857437408,
+    ("F32", "PR", 128, 1): 890018589, ("F32", "PR", 256, 1): 889872329, ("F32", "PR", 512, 1): 890397268,
+    ("F16", "IR", 128, 1): 419228455, ("F16", "IR", 256, 1): 418371397, ("F16", "IR", 512, 1): 418887682,
+    ("F16", "PR", 128, 1): 451110787, ("F16", "PR", 256, 1): 450535906, ("F16", "PR", 512, 1): 450572550,
 }
 KERNEL_FINGERPRINT = "5f8cb9e17b61e9d0"
 KERNEL_SOURCES = ("kernels.cuh", "lattice.cuh", "lbm_internal.h", "fastdiv.h", "kern_d3q27.cu")
@@ -93,14 +93,14 @@ def kernel_fingerprint():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(storage, model, block, override=None):
+def ncu_traffic(storage, model, block, cpt, override=None):
     if override is not None:
         return override
     if KERNEL_FINGERPRINT is None or kernel_fingerprint() != KERNEL_FINGERPRINT:
         return None
     if (LATTICE, NX, NY, NZ) != ("D3Q27", 256, 128, 128):
         return None
-    return NCU_TRAFFIC.get((storage, model, block))
+    return NCU_TRAFFIC.get((storage, model, block, cpt))
 
 
 def measured_hbm_peak():
@@ -234,8 +234,9 @@ def run_ours(args):
         from paper_1610_01388_gb300 import autotune
         for model in ("IR", "PR"):
             best, times = autotune.tune(LATTICE, model, STORAGE, mask.size, steps=200)
-            tuned[model] = {"block": best,
-                            "us_per_step": {str(b): round(t * 1e6, 2) for b, t in times.items()}}
+            tuned[model] = {"block": best[0], "cells_per_thread": best[1],
+                            "us_per_step": {f"{b}x{c}": round(t * 1e6, 2)
+                                            for (b, c), t in times.items()}}
 
     solvers = {}
     for model in ("IR", "PR"):
@@ -288,14 +289,15 @@ def run_ours(args):
                       "mlups": nfluid / t_launch / 1e6}
     dom = "PR" if ms_pr >= ms_ir else "IR"
     roof = {"bound": "hbm",
-            "kernel": f"k_step<{LATTICE},{dom},{STORAGE_CTYPE[STORAGE]}> (dominant by time)",
+            "kernel": (f"{'k_step2' if tuned.get(dom, {}).get('cells_per_thread', 1) == 2 else 'k_step'}"
+                       f"<{LATTICE},{dom},{STORAGE_CTYPE[STORAGE]}> (dominant by time)"),
             "achieved": round(per[dom]["achieved_gbs"], 1), "peak": peak,
             "peak_kind": f"{peak_kind} (copy bandwidth)", "unit": "GB/s",
             "frac": round(per[dom]["frac"], 4),
             "bytes_per_fluid_update": per[dom]["bytes_per_update"],
             "fluid_cells_per_launch": nfluid,
             "traffic": ncu_traffic(STORAGE, dom, tuned.get(dom, {}).get("block", 256),
-                                   args.traffic),
+                                   tuned.get(dom, {}).get("cells_per_thread", 1), args.traffic),
             "per_model": {k: {kk: round(vv, 4) if isinstance(vv, float) else vv
                               for kk, vv in v.items()} for k, v in per.items()}}
     for s in solvers.values():

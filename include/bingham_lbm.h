@@ -262,6 +262,16 @@ lbm_status lbm_tuning_set(lbm_lattice lat, int32_t model, int32_t storage, int32
 /* Block used for a problem of `cells` cells, and its size class. */
 lbm_status lbm_tuning_get(lbm_lattice lat, int32_t model, int32_t storage, int64_t cells,
                           int32_t *block, int32_t *size_class);
+/* Launch shape with the cells each thread steps: 1, or 2 (block 128 or 256;
+ * FP32, FP16 or BF16 storage).  With 2, thread t of a block steps cells
+ * base + t and base + t + block and runs the collision of both at once in
+ * packed two-wide FP32 instructions (fewer issued instructions for the same
+ * arithmetic); results agree with one cell per thread to FP32 round-off.
+ * lbm_tuning_set is lbm_tuning_set_shape with cells_per_thread = 1. */
+lbm_status lbm_tuning_set_shape(lbm_lattice lat, int32_t model, int32_t storage,
+                                int32_t size_class, int32_t block, int32_t cells_per_thread);
+lbm_status lbm_tuning_get_shape(lbm_lattice lat, int32_t model, int32_t storage, int64_t cells,
+                                int32_t *block, int32_t *cells_per_thread, int32_t *size_class);
 lbm_status lbm_tuning_clear(void);   /* also resets the batch schedule below */
 
 /* Batch schedule (no counterpart in the paper), read by every batch (and so

@@ -1,13 +1,16 @@
-"""Autotuner for the step kernel's block size.
+"""Autotuner for the step kernel's launch shape.
 
 For a (lattice, model, storage, size class) it builds a synthetic square duct
-with about 2**size_class cells, times every candidate block size (128, 256,
-512 threads) for a few hundred steps with CUDA events on the solver's stream
-(after a warm-up that also captures the CUDA graphs), takes the fastest, and
-writes it into the library's tuning table (lbm_tuning_set).  Results are
-cached in a JSON file keyed by the GPU name so later processes skip the
-measurement (``load``).  All timing goes through the C ABI; the tuned solver
-arithmetic is the same for every block size, only the launch shape changes.
+with about 2**size_class cells, times every candidate shape (128, 256 or 512
+threads per block at one cell per thread; 128 or 256 at two cells per
+thread, FP32 arithmetic only) for a few hundred steps with CUDA events on
+the solver's stream (after a warm-up that also captures the CUDA graphs),
+takes the fastest, and writes it into the library's tuning table
+(lbm_tuning_set_shape).  Results are cached in a JSON file keyed by the GPU
+name so later processes skip the measurement (``load``).  All timing goes
+through the C ABI.  The block size changes only the launch; two cells per
+thread run the same collision in packed two-wide FP32 instructions (equal to
+FP32 round-off).
 """
 from __future__ import annotations
 
@@ -18,7 +21,8 @@ import os
 from . import lbm
 from . import workloads as W
 
-CANDIDATES = (128, 256, 512)
+# launch shapes (threads per block, cells per thread)
+CANDIDATES = ((128, 1), (256, 1), (512, 1), (128, 2), (256, 2))
 
 
 def _gpu_name():
@@ -36,13 +40,15 @@ def _duct_for(lattice, cells):
 
 
 def measure(lattice, model, storage, size_class, steps=300, warmup=70):
-    """Average step time (s) of every candidate block size."""
+    """Average step time (s) of every candidate launch shape."""
     import torch
     cells = 1 << size_class
     mask = _duct_for(lattice, cells)
     out = {}
-    for block in CANDIDATES:
-        lbm.lbm_tuning_set(lattice, model, storage, size_class, block)
+    for block, cpt in CANDIDATES:
+        if cpt == 2 and storage == "F64":
+            continue
+        lbm.lbm_tuning_set_shape(lattice, model, storage, size_class, block, cpt)
         s = lbm.Solver(lattice, mask, model=model, storage=storage, mu_p=0.1, sigma_y=1e-6,
                        m=1e6, g=(1e-6, 0.0, 0.0), use_torch=True)
         s.step(warmup)
@@ -52,21 +58,23 @@ def measure(lattice, model, storage, size_class, steps=300, warmup=70):
         s.step(steps)
         e1.record(st)
         torch.cuda.synchronize()
-        out[block] = e0.elapsed_time(e1) / 1e3 / steps
+        out[(block, cpt)] = e0.elapsed_time(e1) / 1e3 / steps
         s.close()
     return out
 
 
 def tune(lattice, model, storage, cells, cache=None, steps=300):
-    """Tune the size class of `cells`; returns (best block, {block: seconds})."""
+    """Tune the size class of `cells`; returns (best (block, cells per thread),
+    {(block, cells per thread): seconds})."""
     _, cls = lbm.lbm_tuning_get(lattice, model, storage, cells)
     times = measure(lattice, model, storage, cls, steps=steps)
     best = min(times, key=times.get)
-    lbm.lbm_tuning_set(lattice, model, storage, cls, best)
+    lbm.lbm_tuning_set_shape(lattice, model, storage, cls, *best)
     if cache:
         data = _read(cache)
         data.setdefault(_gpu_name(), {})[f"{lattice}/{model}/{storage}/{cls}"] = {
-            "block": best, "seconds_per_step": times}
+            "block": best[0], "cells_per_thread": best[1],
+            "seconds_per_step": {f"{b}x{c}": t for (b, c), t in times.items()}}
         with open(cache, "w") as fh:
             json.dump(data, fh, indent=1, sort_keys=True)
     return best, times
@@ -84,7 +92,8 @@ def load(cache):
     n = 0
     for key, v in _read(cache).get(_gpu_name(), {}).items():
         lat, model, storage, cls = key.split("/")
-        lbm.lbm_tuning_set(lat, model, storage, int(cls), int(v["block"]))
+        lbm.lbm_tuning_set_shape(lat, model, storage, int(cls), int(v["block"]),
+                                 int(v.get("cells_per_thread", 1)))
         n += 1
     return n
 

@@ -120,6 +120,88 @@ __device__ __forceinline__ uint32_t cvt_rs_bf16x2(float hi, float lo, uint32_t r
 __device__ __forceinline__ void st_u16(void* p, uint32_t v) { *reinterpret_cast<uint16_t*>(p) = (uint16_t)v; }
 
 // ---------------------------------------------------------------------------
+// Two cells in one register pair.  F2 holds one FP32 quantity of two cells;
+// its +, -, * issue the packed f32x2 forms (PTX add/sub/mul/fma .f32x2,
+// sm_100a and later): one instruction for both cells.  A product stays
+// unevaluated (F2P) until it is used, so a following add or subtract becomes
+// one fused multiply-add, the contraction nvcc applies to scalar code.
+struct F2 {
+    unsigned long long v;
+    F2() = default;
+    __device__ __forceinline__ F2(float a) { asm("mov.b64 %0, {%1, %1};" : "=l"(v) : "f"(a)); }
+    __device__ __forceinline__ F2(double a) : F2((float)a) {}
+    __device__ __forceinline__ F2(int a) : F2((float)a) {}
+    __device__ __forceinline__ F2(float a, float b) { asm("mov.b64 %0, {%1, %2};" : "=l"(v) : "f"(a), "f"(b)); }
+    __device__ __forceinline__ float lo() const { return __uint_as_float((unsigned)v); }
+    __device__ __forceinline__ float hi() const { return __uint_as_float((unsigned)(v >> 32)); }
+};
+__device__ __forceinline__ F2 f2_bits(unsigned long long b) {
+    F2 r;
+    r.v = b;
+    return r;
+}
+__device__ __forceinline__ F2 f2_add(F2 a, F2 b) {
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a.v), "l"(b.v));
+    return f2_bits(d);
+}
+__device__ __forceinline__ F2 f2_sub(F2 a, F2 b) {
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a.v), "l"(b.v));
+    return f2_bits(d);
+}
+__device__ __forceinline__ F2 f2_mul(F2 a, F2 b) {
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a.v), "l"(b.v));
+    return f2_bits(d);
+}
+__device__ __forceinline__ F2 f2_fma(F2 a, F2 b, F2 c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a.v), "l"(b.v), "l"(c.v));
+    return f2_bits(d);
+}
+__device__ __forceinline__ F2 operator-(F2 a) { return f2_bits(a.v ^ 0x8000000080000000ull); }
+struct F2P {   // a * b, not yet rounded
+    F2 a, b;
+    __device__ __forceinline__ operator F2() const { return f2_mul(a, b); }
+};
+__device__ __forceinline__ F2 operator+(F2 a, F2 b) { return f2_add(a, b); }
+__device__ __forceinline__ F2 operator-(F2 a, F2 b) { return f2_sub(a, b); }
+__device__ __forceinline__ F2P operator*(F2 a, F2 b) { return F2P{a, b}; }
+__device__ __forceinline__ F2P operator*(F2P p, F2 b) { return F2P{F2(p), b}; }
+__device__ __forceinline__ F2P operator*(F2 a, F2P p) { return F2P{a, F2(p)}; }
+__device__ __forceinline__ F2P operator*(F2P p, F2P q) { return F2P{F2(p), F2(q)}; }
+__device__ __forceinline__ F2 operator+(F2P p, F2 c) { return f2_fma(p.a, p.b, c); }
+__device__ __forceinline__ F2 operator+(F2 c, F2P p) { return f2_fma(p.a, p.b, c); }
+__device__ __forceinline__ F2 operator-(F2 c, F2P p) { return f2_fma(-p.a, p.b, c); }
+__device__ __forceinline__ F2 operator-(F2P p, F2 c) { return f2_fma(p.a, p.b, -c); }
+__device__ __forceinline__ F2 operator+(F2P p, F2P q) { return f2_fma(p.a, p.b, F2(q)); }
+__device__ __forceinline__ F2 operator-(F2P p, F2P q) { return f2_fma(p.a, p.b, -F2(q)); }
+__device__ __forceinline__ F2P operator-(F2P p) { return F2P{-p.a, p.b}; }
+__device__ __forceinline__ F2& operator+=(F2& a, F2 b) { return a = a + b; }
+__device__ __forceinline__ F2& operator-=(F2& a, F2 b) { return a = a - b; }
+__device__ __forceinline__ F2& operator+=(F2& a, F2P p) { return a = a + p; }
+
+// The scalar type of an arithmetic type, and lane access: the parts of the
+// collision with no packed form (sqrt, divisions, expm1, branches) run per
+// cell on the lanes.
+template <class R> struct Lanes {
+    using Sc = R;
+    static constexpr int n = 1;
+    __device__ __forceinline__ static R get(R x, int) { return x; }
+    __device__ __forceinline__ static R make(const R (&v)[1]) { return v[0]; }
+};
+template <> struct Lanes<F2> {
+    using Sc = float;
+    static constexpr int n = 2;
+    __device__ __forceinline__ static float get(F2 x, int k) { return k ? x.hi() : x.lo(); }
+    __device__ __forceinline__ static F2 make(const float (&v)[2]) { return F2(v[0], v[1]); }
+};
+__device__ __forceinline__ float recip(float x) { return 1.0f / x; }
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+__device__ __forceinline__ F2 recip(F2 x) { return F2(1.0f / x.lo(), 1.0f / x.hi()); }
+
+// ---------------------------------------------------------------------------
 // storage.  R is the arithmetic type.  ld / st move population i between
 // memory and registers; enc / dec convert full FP64 populations at the ABI
 // (set/get populations).
@@ -316,44 +398,54 @@ template <class R> struct Mom {
 
 // Grouped sums: populations are added once per velocity class (c_x = +1, -1,
 // 0; c_y = +-1; c_z = +-1; sign of c_x c_y, c_x c_z, c_y c_z) and the moments
-// are sums and differences of those class sums.  Accumulators start at -0.0,
-// the additive identity the compiler may drop.  f is in memory units; beta_i
-// turns each value into an offset (a multiply-add, or a plain add for beta 1).
+// are sums and differences of those class sums.  Each class sum starts as its
+// first member (no add to a zero).  f is in memory units; beta_i turns each
+// value into an offset (a multiply, left out where beta_i = 1).
+enum { kXp, kXm, kX0, kYp, kYm, kZp, kZm, kPxy, kMxy, kPxz, kMxz, kPyz, kMyz, kNumClasses };
+
+__host__ __device__ constexpr bool in_class(int k, int cx, int cy, int cz) {
+    return k == kXp ? cx == 1 : k == kXm ? cx == -1 : k == kX0 ? cx == 0
+         : k == kYp ? cy == 1 : k == kYm ? cy == -1 : k == kZp ? cz == 1 : k == kZm ? cz == -1
+         : k == kPxy ? cx * cy == 1 : k == kMxy ? cx * cy == -1
+         : k == kPxz ? cx * cz == 1 : k == kMxz ? cx * cz == -1
+         : k == kPyz ? cy * cz == 1 : cy * cz == -1;
+}
+template <class L> __host__ __device__ constexpr int first_in_class(int k) {
+    for (int i = 0; i < L::Q; ++i)
+        if (in_class(k, L::cx(i), L::cy(i), L::cz(i))) return i;
+    return -1;
+}
+
 template <class L, class S, class R = typename Store<S>::R>
 __device__ __forceinline__ Mom<R> moments(const R (&f)[L::Q]) {
-    const R z0 = R(-0.0);
-    R xp = z0, xm = z0, x0 = z0, yp = z0, ym = z0, zp = z0, zm = z0;
-    R pxy = z0, mxy = z0, pxz = z0, mxz = z0, pyz = z0, myz = z0;
+    R acc[kNumClasses];
     static_for<0, L::Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
         constexpr int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
-        const R v = f[i] * Store<S>::template beta<L, i>();
-        if constexpr (cx == 1) xp += v;
-        else if constexpr (cx == -1) xm += v;
-        else x0 += v;
-        if constexpr (cy == 1) yp += v;
-        else if constexpr (cy == -1) ym += v;
-        if constexpr (cz == 1) zp += v;
-        else if constexpr (cz == -1) zm += v;
-        if constexpr (cx * cy == 1) pxy += v;
-        else if constexpr (cx * cy == -1) mxy += v;
-        if constexpr (cx * cz == 1) pxz += v;
-        else if constexpr (cx * cz == -1) mxz += v;
-        if constexpr (cy * cz == 1) pyz += v;
-        else if constexpr (cy * cz == -1) myz += v;
+        constexpr auto beta = Store<S>::template beta<L, i>();
+        R v;
+        if constexpr (beta == 1) v = f[i];
+        else v = f[i] * R(beta);
+        static_for<0, kNumClasses>([&](auto K) {
+            constexpr int k = decltype(K)::value;
+            if constexpr (in_class(k, cx, cy, cz)) {
+                if constexpr (first_in_class<L>(k) == i) acc[k] = v;
+                else acc[k] += v;
+            }
+        });
     });
     Mom<R> m;
-    m.xx = xp + xm;
-    m.jx = xp - xm;
-    m.d = m.xx + x0;
-    m.yy = yp + ym;
-    m.jy = yp - ym;
-    m.xy = pxy - mxy;
+    m.xx = acc[kXp] + acc[kXm];
+    m.jx = acc[kXp] - acc[kXm];
+    m.d = m.xx + acc[kX0];
+    m.yy = acc[kYp] + acc[kYm];
+    m.jy = acc[kYp] - acc[kYm];
+    m.xy = acc[kPxy] - acc[kMxy];
     if constexpr (L::D == 3) {
-        m.zz = zp + zm;
-        m.jz = zp - zm;
-        m.xz = pxz - mxz;
-        m.yz = pyz - myz;
+        m.zz = acc[kZp] + acc[kZm];
+        m.jz = acc[kZp] - acc[kZm];
+        m.xz = acc[kPxz] - acc[kMxz];
+        m.yz = acc[kPyz] - acc[kMyz];
     } else {
         m.zz = R(0);
         m.jz = R(0);
@@ -403,26 +495,47 @@ __device__ __forceinline__ R ctc(const Tens<R>& T, R t2xy, R t2xz, R t2yz) {
 }
 
 // ---------------------------------------------------------------------------
-// IR collision (Secs. 2.3, 3.2).  f: memory units in, memory units out.
+// IR yield solve, per cell: s = as T, sigma = asg T (eq. Vikh_sigmaS_tensor)
+// from |T|^2.
+template <class R>
+__device__ __forceinline__ void ir_yield(const Coef<typename Lanes<R>::Sc>& c, R tn2, R& as_out,
+                                         R& asg_out) {
+    using Sc = typename Lanes<R>::Sc;
+    Sc as[Lanes<R>::n], asg[Lanes<R>::n];
+#pragma unroll
+    for (int k = 0; k < Lanes<R>::n; ++k) {
+        const Sc tn = sqrt(Lanes<R>::get(tn2, k));
+        as[k] = Sc(0);
+        asg[k] = Sc(-1);
+        if (tn > Sc(0) && tn >= c.s2y) {
+            const Sc it = Sc(1) / tn;
+            as[k] = -(tn - c.s2y) * c.ir_a * it;
+            asg[k] = -(c.six_nu * tn + c.s2y) * c.ir_b * it;
+        }
+    }
+    as_out = Lanes<R>::make(as);
+    asg_out = Lanes<R>::make(asg);
+}
+
+// ---------------------------------------------------------------------------
+// IR collision (Secs. 2.3, 3.2).  f: memory units in, memory units out.  R is
+// the arithmetic type: one cell (float, double) or two cells (F2).
 template <class L, class S, class R = typename Store<S>::R>
-__device__ __forceinline__ void collide_ir(const Coef<R>& c, uint32_t flags, R (&f)[L::Q],
-                                           R& drho, R (&ur)[3]) {
-    const Mom<R> m = moments<L, S>(f);
+__device__ __forceinline__ void collide_ir(const Coef<typename Lanes<R>::Sc>& c, uint32_t flags,
+                                           R (&f)[L::Q], R& drho, R (&ur)[3]) {
+    const Mom<R> m = moments<L, S, R>(f);
     const R rho = R(1) + m.d;
-    const R inv = R(1) / rho;
-    const R Fx = rho * c.g[0], Fy = rho * c.g[1], Fz = (L::D == 3) ? rho * c.g[2] : R(0);
+    const R inv = recip(rho);
+    const R Fx = rho * R(c.g[0]), Fy = rho * R(c.g[1]);
+    R Fz = R(0);
+    if constexpr (L::D == 3) Fz = rho * R(c.g[2]);
     const R ux = (m.jx + R(0.5) * Fx) * inv;
     const R uy = (m.jy + R(0.5) * Fy) * inv;
-    const R uz = (L::D == 3) ? (m.jz + R(0.5) * Fz) * inv : R(0);
+    R uz = R(0);
+    if constexpr (L::D == 3) uz = (m.jz + R(0.5) * Fz) * inv;
     const Tens<R> T = noneq<L, R>(m, rho, ux, uy, uz, flags);
-    const R tn = sqrt(tnorm2<L, R>(T));
-    // s = as T, sigma = asg T  (eq. Vikh_sigmaS_tensor)
-    R as = R(0), asg = R(-1);
-    if (tn > R(0) && tn >= c.s2y) {
-        const R it = R(1) / tn;
-        as = -(tn - c.s2y) * c.ir_a * it;
-        asg = -(c.six_nu * tn + c.s2y) * c.ir_b * it;
-    }
+    R as, asg;
+    ir_yield<R>(c, tnorm2<L, R>(T), as, asg);
     // A = -sigma_bar + s/2 = k1 T + k2 I with sigma_bar = sigma - tr(sigma)/D I
     const R trT = T.xx + T.yy + T.zz;
     const R k1 = R(0.5) * as - asg;
@@ -436,20 +549,20 @@ __device__ __forceinline__ void collide_ir(const Coef<R>& c, uint32_t flags, R (
     const R t2xy = R(2) * T.xy, t2xz = R(2) * T.xz, t2yz = R(2) * T.yz;
     // odd part: w_i (3 rho c.u + 3/2 c.F) = 3 w_i c.(j + F), since rho u = j + F/2
     const R qx = m.jx + Fx, qy = m.jy + Fy, qz = m.jz + Fz;
-    f[0] = Store<S>::template gam<L, 0>() * (base + R(4.5) * h0);
+    f[0] = R(Store<S>::template gam<L, 0>()) * (base + R(4.5) * h0);
     static_for<0, (L::Q - 1) / 2>([&](auto P) {
         constexpr int i = 2 * decltype(P)::value + 1;
         constexpr int o = i + 1;
         constexpr int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
         constexpr int c2 = cx * cx + cy * cy + cz * cz;
-        const R w = Store<S>::template gam<L, i>();   // w_i in memory units
+        const R w = R(Store<S>::template gam<L, i>());   // w_i in memory units
         // even part e = w (base + 4.5 rho cu^2 + 4.5 h) = A + B cu^2 + C cTc (per class A, B, C)
         const R A = w * (base + R(4.5) * (h0 + k2 * R(c2)));
         const R B = w * r45;
         const R C = w * k145;
         const R cu = cdot<cx, cy, cz>(ux, uy, uz);
         const R e = A + B * (cu * cu) + C * ctc<cx, cy, cz>(T, t2xy, t2xz, t2yz);
-        const R od = Store<S>::template god<L, i>() * cdot<cx, cy, cz>(qx, qy, qz);
+        const R od = R(Store<S>::template god<L, i>()) * cdot<cx, cy, cz>(qx, qy, qz);
         f[i] = e + od;
         f[o] = e - od;
     });
@@ -490,37 +603,59 @@ __device__ __forceinline__ R pr_newton(const Coef<R>& c, R a, R gd, R sy_rho) {
 }
 
 // ---------------------------------------------------------------------------
+// PR relaxation rates, per cell: strain rate with the previous step's tau
+// (or the Newton-implicit one), apparent viscosity, tau and the two TRT rates.
+template <bool IMPLICIT, class R>
+__device__ __forceinline__ void pr_rates(const Coef<typename Lanes<R>::Sc>& c, R tn2, R inv, R& tau,
+                                         R& wp_out, R& wm_out) {
+    using Sc = typename Lanes<R>::Sc;
+    Sc tau_[Lanes<R>::n], wp_[Lanes<R>::n], wm_[Lanes<R>::n];
+#pragma unroll
+    for (int k = 0; k < Lanes<R>::n; ++k) {
+        // D = -T / (2 tau_old c_s^2) = -1.5 T / tau_old ; gdot = sqrt(2 D:D)
+        const Sc tt = sqrt(Sc(2) * Lanes<R>::get(tn2, k));
+        Sc gd = Sc(1.5) / Lanes<R>::get(tau, k) * tt;
+        const Sc sy_rho = c.sigma_y * Lanes<R>::get(inv, k);
+        if constexpr (IMPLICIT) gd = pr_newton(c, Sc(1.5) * tt, gd, sy_rho);
+        Sc nu;
+        if (gd >= c.gdot_c) {
+            nu = c.nu_p + sy_rho * (-expm1(-c.m * gd)) / gd;
+        } else {
+            const Sc nu0 = c.nu_p + c.m * sy_rho;
+            const Sc nuc = c.nu_p + sy_rho * c.e_c;
+            nu = (c.gdot_c - gd) * c.inv_gc * nu0 + gd * c.inv_gc * nuc;
+        }
+        const Sc tn = Sc(0.5) + Sc(3) * nu;
+        wp_[k] = Sc(1) / tn;
+        // 1 / tau_odd with tau_odd = 1/2 + Lambda / (tau - 1/2), as one division
+        const Sc tm = tn - Sc(0.5);
+        wm_[k] = tm / (Sc(0.5) * tm + c.magic);
+        tau_[k] = tn;
+    }
+    tau = Lanes<R>::make(tau_);
+    wp_out = Lanes<R>::make(wp_);
+    wm_out = Lanes<R>::make(wm_);
+}
+
+// ---------------------------------------------------------------------------
 // PR collision (Sec. 3.1 + TRT + EDM).  tau: previous step's relaxation time
 // in, this step's out.  f: memory units in, memory units out (the TRT update is
-// linear and opposite populations share their unit).
+// linear and opposite populations share their unit).  R as for collide_ir.
 template <class L, class S, bool IMPLICIT, class R = typename Store<S>::R>
-__device__ __forceinline__ void collide_pr(const Coef<R>& c, uint32_t flags, R (&f)[L::Q], R& tau,
-                                           R& drho, R (&ur)[3]) {
-    const Mom<R> m = moments<L, S>(f);
+__device__ __forceinline__ void collide_pr(const Coef<typename Lanes<R>::Sc>& c, uint32_t flags,
+                                           R (&f)[L::Q], R& tau, R& drho, R (&ur)[3]) {
+    const Mom<R> m = moments<L, S, R>(f);
     const R rho = R(1) + m.d;
-    const R inv = R(1) / rho;
-    const R ux = m.jx * inv, uy = m.jy * inv, uz = (L::D == 3) ? m.jz * inv : R(0);
+    const R inv = recip(rho);
+    const R ux = m.jx * inv, uy = m.jy * inv;
+    R uz = R(0);
+    if constexpr (L::D == 3) uz = m.jz * inv;
     const Tens<R> T = noneq<L, R>(m, rho, ux, uy, uz, flags);
-    // D = -T / (2 tau_old c_s^2) = -1.5 T / tau_old ; gdot = sqrt(2 D:D)
-    const R tt = sqrt(R(2) * tnorm2<L, R>(T));
-    R gd = R(1.5) / tau * tt;
-    const R sy_rho = c.sigma_y * inv;
-    if constexpr (IMPLICIT) gd = pr_newton(c, R(1.5) * tt, gd, sy_rho);
-    R nu;
-    if (gd >= c.gdot_c) {
-        nu = c.nu_p + sy_rho * (-expm1(-c.m * gd)) / gd;
-    } else {
-        const R nu0 = c.nu_p + c.m * sy_rho;
-        const R nuc = c.nu_p + sy_rho * c.e_c;
-        nu = (c.gdot_c - gd) * c.inv_gc * nu0 + gd * c.inv_gc * nuc;
-    }
-    const R tn = R(0.5) + R(3) * nu;
-    const R wp = R(1) / tn;
-    // 1 / tau_odd with tau_odd = 1/2 + Lambda / (tau - 1/2), as one division
-    const R tm = tn - R(0.5);
-    const R wm = tm / (R(0.5) * tm + c.magic);
-    tau = tn;
-    const R gx = c.g[0], gy = c.g[1], gz = (L::D == 3) ? c.g[2] : R(0);
+    R wp, wm;
+    pr_rates<IMPLICIT, R>(c, tnorm2<L, R>(T), inv, tau, wp, wm);
+    const R gx = R(c.g[0]), gy = R(c.g[1]);
+    R gz = R(0);
+    if constexpr (L::D == 3) gz = R(c.g[2]);
     const R Fx = rho * gx, Fy = rho * gy, Fz = rho * gz;
     const R uu = ux * ux + uy * uy + uz * uz;
     const R ug = ux * gx + uy * gy + uz * gz;
@@ -529,15 +664,15 @@ __device__ __forceinline__ void collide_pr(const Coef<R>& c, uint32_t flags, R (
     const R fbase = R(-1.5) * rho * (R(2) * ug + gg);      // even part of the EDM difference
     const R r45 = R(4.5) * rho;
     {
-        const R w0 = Store<S>::template gam<L, 0>();
+        const R w0 = R(Store<S>::template gam<L, 0>());
         f[0] = f[0] - wp * (f[0] - w0 * base) + w0 * fbase;
     }
     static_for<0, (L::Q - 1) / 2>([&](auto P) {
         constexpr int i = 2 * decltype(P)::value + 1;
         constexpr int o = i + 1;
         constexpr int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
-        const R w = Store<S>::template gam<L, i>();    // w_i and 3 w_i in memory units
-        const R w3 = Store<S>::template god<L, i>();
+        const R w = R(Store<S>::template gam<L, i>());    // w_i and 3 w_i in memory units
+        const R w3 = R(Store<S>::template god<L, i>());
         const R cu = cdot<cx, cy, cz>(ux, uy, uz);
         const R cg = cdot<cx, cy, cz>(gx, gy, gz);
         const R fe = R(0.5) * (f[i] + f[o]);
@@ -682,6 +817,87 @@ k_step(const KArgs a, const SrcPlanes<S> src, const DstPlanes<S> dst,
     }
     if (active) cell_step<L, MODEL, S, CHECK>(kp, coef<R>(a), src, dst, lk, idx, tau, usnap, rnd, acc);
     if constexpr (CHECK) block_sum_store(acc, partials + (int64_t)blockIdx.x * kNumStats);
+}
+
+// ---------------------------------------------------------------------------
+// Two cells per thread.  Thread t of a block works on cells base + t and
+// base + t + BLOCK, so every load and store instruction of a warp stays
+// contiguous; it gathers and stores each cell as cell_step does and runs one
+// collision on F2 values (packed f32x2 arithmetic for both cells).  A lane
+// whose cell is solid or past the end repeats the other cell's work and
+// stores nothing.  Plain steps of the FP32 and 16-bit forms only.
+template <class L, int MODEL, class S, class Src, class Dst>
+__device__ __forceinline__ void cell_step2(const KParams& kp, const Coef<float>& c, const Src& src,
+                                           const Dst& dst, const uint32_t (&lk)[2],
+                                           const int (&idx)[2], const bool (&act)[2],
+                                           float* __restrict__ tau, const uint32_t (&rnd)[2]) {
+    float a[L::Q], b[L::Q];
+    gather<L, S>(kp, src, lk[0], idx[0], a);
+    gather<L, S>(kp, src, lk[1], idx[1], b);
+    F2 f[L::Q];
+    static_for<0, L::Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        f[i] = F2(a[i], b[i]);
+    });
+    F2 drho, ur[3];
+    if constexpr (MODEL != LBM_MODEL_IR) {
+        F2 t(tau[idx[0]], tau[idx[1]]);
+        collide_pr<L, S, MODEL == kModelPRImplicit, F2>(c, kp.flags, f, t, drho, ur);
+        if (act[0]) tau[idx[0]] = t.lo();
+        if (act[1]) tau[idx[1]] = t.hi();
+    } else {
+        collide_ir<L, S, F2>(c, kp.flags, f, drho, ur);
+    }
+    static_for<0, 2>([&](auto K) {
+        constexpr int k = decltype(K)::value;
+        if (act[k]) {
+            const int n = idx[k];
+            Store<S>::template st<L, 0>(dst.template at<0>(n), Lanes<F2>::get(f[0], k), rnd[k]);
+            static_for<0, (L::Q - 1) / 2>([&](auto P) {
+                constexpr int i = 2 * decltype(P)::value + 1;
+                Store<S>::template st2<L, i>(dst.template at<i>(n), dst.template at<i + 1>(n),
+                                             Lanes<F2>::get(f[i], k), Lanes<F2>::get(f[i + 1], k),
+                                             pair_bits<decltype(P)::value + 1>(rnd[k]));
+            });
+        }
+    });
+}
+
+// PR: at most 128 registers a thread, so 16 warps (1024 cells) stay resident
+// per SM, the memory-level parallelism of the one-cell PR kernel.  IR needs
+// fewer registers unbounded.
+template <int MODEL, int BLOCK> constexpr int step2_min_blocks() {
+    return MODEL == LBM_MODEL_IR ? 0 : 512 / BLOCK;
+}
+
+template <class L, int MODEL, class S, int BLOCK>
+__global__ void __launch_bounds__(BLOCK, step2_min_blocks<MODEL, BLOCK>())
+k_step2(const KArgs a, const SrcPlanes<S> src, const DstPlanes<S> dst,
+        const uint32_t* __restrict__ links, float* __restrict__ tau,
+        uint32_t* __restrict__ rng_ctr, int parity) {
+    static_assert(std::is_same<typename Store<S>::R, float>::value, "two-cell steps need FP32 arithmetic");
+    const KParams& kp = a.kp;
+    const int i0 = blockIdx.x * (2 * BLOCK) + threadIdx.x;
+    const int i1 = i0 + BLOCK;
+    uint32_t seed = 0u;
+    if constexpr (Store<S>::kStochastic) {
+        // this launch reads counter[parity] and leaves counter + 1 for the next
+        seed = __ldg(rng_ctr + parity);
+        if (blockIdx.x == 0 && threadIdx.x == 0) rng_ctr[parity ^ 1] = seed + 1u;
+    }
+    const uint32_t l0 = i0 < kp.ncells ? __ldg(links + i0) : kSolidBit;
+    const uint32_t l1 = i1 < kp.ncells ? __ldg(links + i1) : kSolidBit;
+    const bool a0 = !(l0 & kSolidBit), a1 = !(l1 & kSolidBit);
+    if (!a0 && !a1) return;
+    const int idx[2] = {a0 ? i0 : i1, a1 ? i1 : i0};
+    const uint32_t lk[2] = {a0 ? l0 : l1, a1 ? l1 : l0};
+    const bool act[2] = {a0, a1};
+    uint32_t rnd[2] = {0u, 0u};
+    if constexpr (Store<S>::kStochastic) {
+        rnd[0] = pcg_hash((uint32_t)idx[0] ^ (seed * 0x9e3779b9u));
+        rnd[1] = pcg_hash((uint32_t)idx[1] ^ (seed * 0x9e3779b9u));
+    }
+    cell_step2<L, MODEL, S>(kp, a.cf, src, dst, lk, idx, act, tau, rnd);
 }
 
 // ---------------------------------------------------------------------------
@@ -933,6 +1149,17 @@ cudaError_t launch_step_t(bool check, const KParams& kp, const StepArgs& s, cuda
     const SrcPlanes<S> src = src_planes<L, S>(s.fsrc, kp.plane);
     const DstPlanes<S> dst = dst_planes<L, S>(s.fdst, kp.plane);
     const int block = (check || MODEL == kModelPRImplicit) ? kBlock : s.block;   // implicit: untuned
+    if constexpr (MODEL != kModelPRImplicit && std::is_same<typename Store<S>::R, float>::value) {
+        if (!check && s.cpt == 2) {   // two cells per thread
+            if (block == 128)
+                k_step2<L, MODEL, S, 128><<<(kp.ncells + 255) / 256, 128, 0, st>>>(
+                    a, src, dst, s.links, (R*)s.tau, s.rng_ctr, s.parity);
+            else
+                k_step2<L, MODEL, S, 256><<<(kp.ncells + 511) / 512, 256, 0, st>>>(
+                    a, src, dst, s.links, (R*)s.tau, s.rng_ctr, s.parity);
+            return cudaGetLastError();
+        }
+    }
     if (check) {
         k_step<L, MODEL, S, true><<<grid, kBlock, 0, st>>>(
             a, src, dst, s.links, (R*)s.tau, (R*)s.usnap, s.partials, s.rng_ctr, s.parity);

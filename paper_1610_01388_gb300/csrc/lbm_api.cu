@@ -170,6 +170,7 @@ cudaError_t launch_step(lbm_solver* s, bool check, cudaStream_t st) {
     a.rng_ctr = (uint32_t*)(s->stats + 2 * kNumStats);
     a.parity = s->cur;
     a.block = s->block;
+    a.cpt = s->cpt;
     const int km = kernel_model(s->p.model, s->kp.newton);
     switch (s->lat) {
     case LBM_D2Q9: return launch_step_D2Q9(km, s->p.storage, check, s->kp, a, st);
@@ -531,13 +532,18 @@ lbm_status lbm_create_with_workspace(lbm_solver** out, lbm_lattice lat, int nx, 
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
-// Tuning table: threads per block of the plain step kernel per (lattice,
-// model, storage, size class = floor(log2 cells)); filled by the autotuner
-// through lbm_tuning_set, read by every solver before it steps.
+// Tuning table: launch shape of the plain step kernel (threads per block,
+// cells per thread) per (lattice, model, storage, size class =
+// floor(log2 cells)); filled by the autotuner through lbm_tuning_set(_shape),
+// read by every solver before it steps.
 namespace {
 
+struct Shape {
+    int block = kBlock, cpt = 1;
+};
+
 std::mutex g_tune_mu;
-std::map<uint64_t, int> g_tune;
+std::map<uint64_t, Shape> g_tune;
 std::atomic<uint64_t> g_tune_version{0};
 
 int size_class(int64_t cells) {
@@ -550,26 +556,45 @@ uint64_t tune_key(int lat, int model, int storage, int cls) {
     return ((uint64_t)lat << 24) | ((uint64_t)model << 16) | ((uint64_t)storage << 8) | (uint64_t)cls;
 }
 
-int tune_lookup(int lat, int model, int storage, int64_t cells) {
+Shape tune_lookup(int lat, int model, int storage, int64_t cells) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune.find(tune_key(lat, model, storage, size_class(cells)));
-    return it == g_tune.end() ? kBlock : it->second;
+    return it == g_tune.end() ? Shape{} : it->second;
 }
 
-// Adopt the current table; a changed block size invalidates captured graphs.
+// Adopt the current table; a changed launch shape invalidates captured graphs.
 void apply_tuning(lbm_solver* s) {
     const uint64_t ver = g_tune_version.load();
     if (s->tune_version == ver) return;
-    const int b = tune_lookup(s->lat, s->p.model, s->p.storage, s->ncells);
-    if (b != s->block) {
+    const Shape sh = tune_lookup(s->lat, s->p.model, s->p.storage, s->ncells);
+    if (sh.block != s->block || sh.cpt != s->cpt) {
         for (int k = 0; k < 2; ++k)
             if (s->graph[k]) {
                 cudaGraphExecDestroy(s->graph[k]);
                 s->graph[k] = nullptr;
             }
-        s->block = b;
+        s->block = sh.block;
+        s->cpt = sh.cpt;
     }
     s->tune_version = ver;
+}
+
+lbm_status set_shape(int lat, int32_t model, int32_t storage, int32_t cls, int32_t block,
+                     int32_t cpt) {
+    if (lattice_q(lat) == 0) return fail(LBM_EINVAL, "unknown lattice %d", lat);
+    if (model != LBM_MODEL_PR && model != LBM_MODEL_IR) return fail(LBM_EINVAL, "unknown model %d", model);
+    if (storage_bytes(storage) == 0) return fail(LBM_EINVAL, "unknown storage %d", storage);
+    if (cls < 0 || cls > 62) return fail(LBM_EINVAL, "size class must be in 0..62");
+    if (block != 128 && block != 256 && block != 512) return fail(LBM_EINVAL, "block must be 128, 256 or 512");
+    if (cpt != 1 && cpt != 2) return fail(LBM_EINVAL, "cells per thread must be 1 or 2");
+    if (cpt == 2 && block == 512) return fail(LBM_EINVAL, "two cells per thread need block 128 or 256");
+    if (cpt == 2 && storage == LBM_F64) return fail(LBM_EINVAL, "two cells per thread need FP32 arithmetic (not LBM_F64)");
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune[tune_key(lat, model, storage, cls)] = Shape{block, cpt};
+    }
+    g_tune_version.fetch_add(1);
+    return LBM_OK;
 }
 
 }  // namespace
@@ -578,23 +603,25 @@ extern "C" {
 
 lbm_status lbm_tuning_set(lbm_lattice lat, int32_t model, int32_t storage, int32_t size_class_,
                           int32_t block) {
-    if (lattice_q(lat) == 0) return fail(LBM_EINVAL, "unknown lattice %d", (int)lat);
-    if (model != LBM_MODEL_PR && model != LBM_MODEL_IR) return fail(LBM_EINVAL, "unknown model %d", model);
-    if (storage_bytes(storage) == 0) return fail(LBM_EINVAL, "unknown storage %d", storage);
-    if (size_class_ < 0 || size_class_ > 62) return fail(LBM_EINVAL, "size class must be in 0..62");
-    if (block != 128 && block != 256 && block != 512) return fail(LBM_EINVAL, "block must be 128, 256 or 512");
-    {
-        std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tune[tune_key(lat, model, storage, size_class_)] = block;
-    }
-    g_tune_version.fetch_add(1);
-    return LBM_OK;
+    return set_shape(lat, model, storage, size_class_, block, 1);
+}
+
+lbm_status lbm_tuning_set_shape(lbm_lattice lat, int32_t model, int32_t storage,
+                                int32_t size_class_, int32_t block, int32_t cells_per_thread) {
+    return set_shape(lat, model, storage, size_class_, block, cells_per_thread);
 }
 
 lbm_status lbm_tuning_get(lbm_lattice lat, int32_t model, int32_t storage, int64_t cells,
                           int32_t* block, int32_t* size_class_) {
+    return lbm_tuning_get_shape(lat, model, storage, cells, block, nullptr, size_class_);
+}
+
+lbm_status lbm_tuning_get_shape(lbm_lattice lat, int32_t model, int32_t storage, int64_t cells,
+                                int32_t* block, int32_t* cells_per_thread, int32_t* size_class_) {
     if (lattice_q(lat) == 0 || cells < 1) return fail(LBM_EINVAL, "bad lattice or cell count");
-    if (block) *block = tune_lookup(lat, model, storage, cells);
+    const Shape sh = tune_lookup(lat, model, storage, cells);
+    if (block) *block = sh.block;
+    if (cells_per_thread) *cells_per_thread = sh.cpt;
     if (size_class_) *size_class_ = size_class(cells);
     return LBM_OK;
 }

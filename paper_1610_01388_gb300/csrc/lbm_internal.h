@@ -50,6 +50,7 @@ struct StepArgs {
     uint32_t* rng_ctr;   // 16-bit storage: launch counters for stochastic rounding [2]
     int parity;          // which of the two counters this launch reads
     int block;           // threads per block of plain steps (128, 256 or 512)
+    int cpt;             // cells per thread of plain steps (1, or 2 with block 128 / 256)
 };
 
 enum ReduceMode { kReduceFlow = 0, kReduceTotals = 1 };

@@ -61,5 +61,6 @@ struct lbm_solver {
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     int graph_len = 64;
     int block = 256;                   // threads per block of plain steps (tuning table)
+    int cpt = 1;                       // cells per thread of plain steps (tuning table)
     uint64_t tune_version = ~uint64_t(0);
 };

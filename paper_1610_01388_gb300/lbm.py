@@ -41,7 +41,8 @@ EXPORTED = ["lbm_params_default", "lbm_lattice_info", "lbm_workspace_bytes", "lb
             "lbm_server_create", "lbm_server_submit", "lbm_server_advance", "lbm_server_result",
             "lbm_server_fields", "lbm_server_pending", "lbm_server_now", "lbm_server_destroy",
             "lbm_tuning_set", "lbm_tuning_get", "lbm_tuning_clear", "lbm_set_wait_limit",
-            "lbm_get_wait_limit", "lbm_get_populations_cells", "lbm_tuning_set_batch", "lbm_tuning_get_batch",
+            "lbm_get_wait_limit", "lbm_get_populations_cells", "lbm_tuning_set_shape",
+            "lbm_tuning_get_shape", "lbm_tuning_set_batch", "lbm_tuning_get_batch",
             "lbm_tuning_set_batch_concurrency", "lbm_tuning_get_batch_concurrency"]
 LBM_REQ_QUEUED, LBM_REQ_RUNNING, LBM_REQ_CONVERGED, LBM_REQ_CAPPED, LBM_REQ_FAILED = range(5)
 
@@ -143,6 +144,8 @@ def library():
             "lbm_tuning_set": [i32, i32, i32, i32, i32],
             "lbm_tuning_get": [i32, i32, i32, i64, P(i32), P(i32)],
             "lbm_tuning_clear": [],
+            "lbm_tuning_set_shape": [i32, i32, i32, i32, i32, i32],
+            "lbm_tuning_get_shape": [i32, i32, i32, i64, P(i32), P(i32), P(i32)],
             "lbm_set_wait_limit": [ctypes.c_double],
             "lbm_get_populations_cells": [vp, vp, i64, vp],
             "lbm_tuning_set_batch": [i32, i32, i32, i32],
@@ -345,6 +348,19 @@ def lbm_tuning_get(lat, model, storage, cells):
 
 def lbm_tuning_clear():
     _check(library().lbm_tuning_clear())
+
+
+def lbm_tuning_set_shape(lat, model, storage, size_class, block, cells_per_thread):
+    _check(library().lbm_tuning_set_shape(_lat(lat), _mdl(model), _sto(storage), int(size_class),
+                                          int(block), int(cells_per_thread)))
+
+
+def lbm_tuning_get_shape(lat, model, storage, cells):
+    """(block, cells per thread, size class) the library uses for `cells` cells."""
+    b, c, k = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(library().lbm_tuning_get_shape(_lat(lat), _mdl(model), _sto(storage), int(cells),
+                                          ctypes.byref(b), ctypes.byref(c), ctypes.byref(k)))
+    return b.value, c.value, k.value
 
 
 def lbm_tuning_set_batch(lat, model, storage, ctas_per_sm):

@@ -144,6 +144,24 @@ def test_tuning_table_host_logic():
     assert lbm.lbm_tuning_get("D3Q27", "IR", "F32", 5_000_000)[0] == 256
 
 
+def test_tuning_shape_host_logic():
+    lbm.lbm_tuning_clear()
+    assert lbm.lbm_tuning_get_shape("D3Q27", "PR", "F32", 4_194_304) == (256, 1, 22)
+    lbm.lbm_tuning_set_shape("D3Q27", "PR", "F32", 22, 128, 2)
+    assert lbm.lbm_tuning_get_shape("D3Q27", "PR", "F32", 5_000_000) == (128, 2, 22)
+    assert lbm.lbm_tuning_get("D3Q27", "PR", "F32", 5_000_000) == (128, 22)
+    lbm.lbm_tuning_set("D3Q27", "PR", "F32", 22, 512)          # plain set: one cell per thread
+    assert lbm.lbm_tuning_get_shape("D3Q27", "PR", "F32", 5_000_000) == (512, 1, 22)
+    lib = lbm.library()
+    assert lib.lbm_tuning_set_shape(3, 0, 1, 22, 512, 2) == lbm.LBM_EINVAL    # 512 x 2
+    assert lib.lbm_tuning_set_shape(3, 0, 0, 22, 128, 2) == lbm.LBM_EINVAL    # F64
+    assert lib.lbm_tuning_set_shape(3, 0, 1, 22, 128, 3) == lbm.LBM_EINVAL
+    lbm.lbm_tuning_set_shape("D2Q9", "IR", "F16", 10, 256, 2)
+    assert lbm.lbm_tuning_get_shape("D2Q9", "IR", "F16", 1500) == (256, 2, 10)
+    lbm.lbm_tuning_clear()
+    assert lbm.lbm_tuning_get_shape("D2Q9", "IR", "F16", 1500) == (256, 1, 10)
+
+
 def test_batch_schedule_host_logic():
     lbm.lbm_tuning_clear()
     assert lbm.lbm_tuning_get_batch("D3Q27", "PR", "F16") == 0

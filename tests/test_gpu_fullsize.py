@@ -68,6 +68,23 @@ def test_fullsize_square_duct(lat, model):
 
 
 @pytest.mark.parametrize("model", ["PR", "IR"])
+@pytest.mark.parametrize("block", [128, 256])
+def test_fullsize_square_duct_two_cells_per_thread(model, block):
+    """The bench duct (D3Q27, 256 x 128 x 128) with plain steps at two cells
+    per thread, a launch shape the autotuner may pick for the bench."""
+    prm = W.duct_params(H=127, nu_p=0.1, u_newton=0.02, bn=2.0)
+    mask = W.duct_mask(256, 128, 128)
+    lbm.lbm_tuning_clear()
+    try:
+        _, _, cls = lbm.lbm_tuning_get_shape("D3Q27", model, "F32", mask.size)
+        lbm.lbm_tuning_set_shape("D3Q27", model, "F32", cls, block, 2)
+        _sampled_step_parity("D3Q27", mask, model, 300, nu_p=0.1, sigma_y=prm["sigma_y"], m=1e6,
+                             g=(prm["g"], 0.0, 0.0))
+    finally:
+        lbm.lbm_tuning_clear()
+
+
+@pytest.mark.parametrize("model", ["PR", "IR"])
 def test_fullsize_porous_d3q19(model):
     """Porous box 256^3, random non-overlapping spheres r in [6, 10], porosity
     0.7, seed 1, body-force driven."""

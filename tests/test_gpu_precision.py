@@ -13,6 +13,7 @@ import numpy as np
 import pytest
 
 import oracle
+from paper_1610_01388_gb300 import lbm
 from paper_1610_01388_gb300 import workloads as W
 
 from _pairs import gpu_to_oracle, make_pair, oracle_to_gpu, rel_l2_u, set_both
@@ -88,4 +89,21 @@ def test_duct_velocity_error(storage, model):
 def test_porous_velocity_error(storage, model):
     err = _porous_case(storage, model)
     print(f"porous D3Q27 {model} {storage}: rel L2 u error {err:.3e}")
+    assert err <= BAR[storage]
+
+
+@pytest.mark.parametrize("storage", ["F16", "BF16"])
+@pytest.mark.parametrize("model", ["PR", "IR"])
+def test_duct_velocity_error_two_cells_per_thread(storage, model):
+    """The same bar with plain steps at two cells per thread (packed FP32
+    collision of both cells)."""
+    mask_cells = 16 * 25 * 25
+    lbm.lbm_tuning_clear()
+    try:
+        _, _, cls = lbm.lbm_tuning_get_shape("D3Q27", model, storage, mask_cells)
+        lbm.lbm_tuning_set_shape("D3Q27", model, storage, cls, 128, 2)
+        err = _duct_case(storage, model)
+    finally:
+        lbm.lbm_tuning_clear()
+    print(f"duct D3Q27 {model} {storage} 2 cells/thread: rel L2 u error {err:.3e}")
     assert err <= BAR[storage]
