@@ -302,6 +302,8 @@ template <class R> struct Coef {
     R ir_b;    // 1 / (1 + 6 nu_p)
     R six_nu;  // 6 nu_p
     int newton;  // PR: Newton iterations of the implicit tau update
+    R cg[13];   // c_i . g of direction i = 2p + 1 (PR force terms), per pair p
+    R cgg[13];  // (c_i . g)^2
 };
 
 struct KArgs {
@@ -663,28 +665,32 @@ __device__ __forceinline__ void collide_pr(const Coef<typename Lanes<R>::Sc>& c,
     const R base = m.d - R(1.5) * rho * uu;                 // even part of f_eq - w, direction-free
     const R fbase = R(-1.5) * rho * (R(2) * ug + gg);      // even part of the EDM difference
     const R r45 = R(4.5) * rho;
+    // Per pair (i, o = opposite), with f^+- = (f_i +- f_o) / 2:
+    //   E = f^+ - wp (f^+ - f_eq^+) + F^+ = (1 - wp)/2 (f_i + f_o) + w_i (K0 + 4.5 rho t),
+    //       K0 = wp base + fbase,  t = wp cu^2 + cg (2 cu + cg) = cu (wp cu + 2 cg) + cg^2;
+    //   O = f^- - wm (f^- - f_eq^-) + F^- = (1 - wm)/2 (f_i - f_o) + 3 w_i c.(wm j + F),
+    // the odd equilibrium and force parts from j and F directly (3 w_i rho c.u
+    // = 3 w_i c.j exactly).  cg = c_i.g and cg^2 are per-launch constants.
+    const R omp = R(0.5) - R(0.5) * wp;
+    const R omm = R(0.5) - R(0.5) * wm;
+    const R K0 = wp * base + fbase;
+    const R qx = wm * m.jx + Fx, qy = wm * m.jy + Fy, qz = wm * m.jz + Fz;
     {
         const R w0 = R(Store<S>::template gam<L, 0>());
-        f[0] = f[0] - wp * (f[0] - w0 * base) + w0 * fbase;
+        f[0] = (R(1) - wp) * f[0] + w0 * K0;
     }
     static_for<0, (L::Q - 1) / 2>([&](auto P) {
-        constexpr int i = 2 * decltype(P)::value + 1;
+        constexpr int p = decltype(P)::value;
+        constexpr int i = 2 * p + 1;
         constexpr int o = i + 1;
         constexpr int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
         const R w = R(Store<S>::template gam<L, i>());    // w_i and 3 w_i in memory units
         const R w3 = R(Store<S>::template god<L, i>());
         const R cu = cdot<cx, cy, cz>(ux, uy, uz);
-        const R cg = cdot<cx, cy, cz>(gx, gy, gz);
-        const R fe = R(0.5) * (f[i] + f[o]);
-        const R fo = R(0.5) * (f[i] - f[o]);
-        const R wr = w * r45;
-        const R eqe = w * base + wr * (cu * cu);
-        // odd parts from j and F directly: 3 w_i rho c.u = 3 w_i c.j exactly
-        const R eqo = w3 * cdot<cx, cy, cz>(m.jx, m.jy, m.jz);
-        const R Fe = w * fbase + wr * (cg * (R(2) * cu + cg));
-        const R Fo = w3 * cdot<cx, cy, cz>(Fx, Fy, Fz);
-        const R E = fe - wp * (fe - eqe) + Fe;
-        const R O = fo - wm * (fo - eqo) + Fo;
+        const R cg = R(c.cg[p]);
+        const R t = cu * (wp * cu + R(2) * cg) + R(c.cgg[p]);
+        const R E = omp * (f[i] + f[o]) + w * (K0 + r45 * t);
+        const R O = omm * (f[i] - f[o]) + w3 * cdot<cx, cy, cz>(qx, qy, qz);
         f[i] = E + O;
         f[o] = E - O;
     });
@@ -1103,6 +1109,19 @@ k_gather_cells(const KParams kp, const S* __restrict__ f, const int64_t* __restr
 
 // ---------------------------------------------------------------------------
 // host-side helpers for the per-lattice launchers
+template <class L, class R> inline void fill_force_dirs(Coef<R>& c, const KParams& kp) {
+    for (int p = 0; p < 13; ++p) {
+        c.cg[p] = R(0);
+        c.cgg[p] = R(0);
+    }
+    for (int p = 0; p < (L::Q - 1) / 2; ++p) {
+        const int i = 2 * p + 1;
+        const double cg = L::cx(i) * kp.g[0] + L::cy(i) * kp.g[1] + L::cz(i) * kp.g[2];
+        c.cg[p] = (R)cg;
+        c.cgg[p] = (R)(cg * cg);
+    }
+}
+
 template <class R> inline Coef<R> make_coef(const KParams& kp) {
     Coef<R> c;
     const double nu = kp.nu_p;
@@ -1122,12 +1141,27 @@ template <class R> inline Coef<R> make_coef(const KParams& kp) {
     return c;
 }
 
-inline KArgs make_args(const KParams& kp) {
+template <class L> inline KArgs make_args(const KParams& kp) {
     KArgs a;
     a.kp = kp;
     a.cf = make_coef<float>(kp);
     a.cd = make_coef<double>(kp);
+    fill_force_dirs<L>(a.cf, kp);
+    fill_force_dirs<L>(a.cd, kp);
     return a;
+}
+
+// Coefficients of a domain of lattice `lat` (host code without the lattice
+// as a template parameter: the batch tables).
+template <class R> inline Coef<R> make_coef_lat(const KParams& kp, int lat) {
+    Coef<R> c = make_coef<R>(kp);
+    switch (lat) {
+    case LBM_D2Q9: fill_force_dirs<D2Q9>(c, kp); break;
+    case LBM_D3Q15: fill_force_dirs<D3Q15>(c, kp); break;
+    case LBM_D3Q19: fill_force_dirs<D3Q19>(c, kp); break;
+    default: fill_force_dirs<D3Q27>(c, kp); break;
+    }
+    return c;
 }
 
 template <class L, class S> inline SrcPlanes<S> src_planes(const void* f, int64_t plane) {
@@ -1144,7 +1178,7 @@ template <class L, class S> inline DstPlanes<S> dst_planes(void* f, int64_t plan
 template <class L, int MODEL, class S>
 cudaError_t launch_step_t(bool check, const KParams& kp, const StepArgs& s, cudaStream_t st) {
     using R = typename Store<S>::R;
-    const KArgs a = make_args(kp);
+    const KArgs a = make_args<L>(kp);
     const int grid = step_grid(kp.ncells);
     const SrcPlanes<S> src = src_planes<L, S>(s.fsrc, kp.plane);
     const DstPlanes<S> dst = dst_planes<L, S>(s.fdst, kp.plane);
@@ -1244,7 +1278,7 @@ cudaError_t launch_links_lat(const KParams& kp, const uint8_t* mask, uint32_t* l
 template <class L>
 cudaError_t launch_fields_lat(int storage, const KParams& kp, const void* f, const uint32_t* links,
                               double* rho, double* ux, double* uy, double* uz, cudaStream_t st) {
-    const KArgs a = make_args(kp);
+    const KArgs a = make_args<L>(kp);
     const int grid = step_grid(kp.ncells);
     switch (storage) {
     case LBM_F32:
@@ -1279,7 +1313,7 @@ template <class L>
 cudaError_t launch_reduce_lat(int storage, int mode, const KParams& kp, const void* f,
                               const uint32_t* links, double* partials, int nblocks,
                               cudaStream_t st) {
-    const KArgs a = make_args(kp);
+    const KArgs a = make_args<L>(kp);
     switch (storage) {
     case LBM_F32: return launch_reduce_s<L, float>(mode, a, f, links, partials, nblocks, st);
     case LBM_F64: return launch_reduce_s<L, double>(mode, a, f, links, partials, nblocks, st);

@@ -229,8 +229,8 @@ lbm_status rebuild(lbm_batch* b) {
             BatchDesc& D = desc[j];
             std::memset(&D, 0, sizeof(D));
             D.kp = s->kp;
-            D.cf = make_coef<float>(s->kp);
-            D.cd = make_coef<double>(s->kp);
+            D.cf = make_coef_lat<float>(s->kp, s->lat);
+            D.cd = make_coef_lat<double>(s->kp, s->lat);
             D.f[0] = s->f[0];
             D.f[1] = s->f[1];
             D.links = s->links;
