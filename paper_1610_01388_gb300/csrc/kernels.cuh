@@ -702,12 +702,15 @@ __device__ __forceinline__ void collide_pr(const Coef<typename Lanes<R>::Sc>& c,
 
 // ---------------------------------------------------------------------------
 // deterministic block reduction of kNumStats values (fixed shuffle tree).
-// The warp stage runs in the type of v (the arithmetic type on check steps,
-// which keeps FP32 paths off the low-rate FP64 pipe); the sums across warps
-// and blocks are FP64.
+// The warp and block stages run in the type of v (the arithmetic type on
+// check steps: at most 256 terms); each block's sums are stored as FP64
+// partials and summed in FP64 in a fixed order by the finaliser.  Keeping the
+// block stage off the FP64 pipe matters on GB300, whose FP64 rate is a small
+// fraction of FP32: a serial FP64 shuffle chain per block made check steps
+// four to five times slower than plain steps.
 template <class V>
 __device__ __forceinline__ void block_sum_store(V (&v)[kNumStats], double* __restrict__ out) {
-    __shared__ double sm[kBlock / 32][kNumStats];
+    __shared__ V sm[kBlock / 32][kNumStats];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < kNumStats; ++k) {
@@ -716,16 +719,16 @@ __device__ __forceinline__ void block_sum_store(V (&v)[kNumStats], double* __res
     }
     if (lane == 0) {
 #pragma unroll
-        for (int k = 0; k < kNumStats; ++k) sm[warp][k] = (double)v[k];
+        for (int k = 0; k < kNumStats; ++k) sm[warp][k] = v[k];
     }
     __syncthreads();
     if (warp == 0) {
 #pragma unroll
         for (int k = 0; k < kNumStats; ++k) {
-            double t = (lane < kBlock / 32) ? sm[lane][k] : 0.0;
+            V t = (lane < kBlock / 32) ? sm[lane][k] : V(0);
 #pragma unroll
             for (int o = 4; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
-            if (lane == 0) out[k] = t;
+            if (lane == 0) out[k] = (double)t;
         }
     }
 }
@@ -755,6 +758,14 @@ __device__ __forceinline__ void cell_step(const KParams& kp, const Coef<typename
                                           typename Store<S>::R* __restrict__ usnap, uint32_t rnd,
                                           typename Store<S>::R (&acc)[kNumStats]) {
     using R = typename Store<S>::R;
+    // check steps: the previous snapshot is read first, so its latency overlaps
+    // the gather (after the population stores the compiler could not move
+    // these loads up past them: the pointers may alias)
+    R up[3] = {R(0), R(0), R(0)};
+    if constexpr (CHECK) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) up[d] = usnap[(int64_t)d * kp.plane + idx];
+    }
     R f[L::Q];
     gather<L, S>(kp, src, lk, idx, f);
     R drho, ur[3];
@@ -777,9 +788,8 @@ __device__ __forceinline__ void cell_step(const KParams& kp, const Coef<typename
         R du2 = R(0), u2 = R(0);
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            const R up = usnap[(int64_t)d * plane + idx];
             acc[kStatUx + d] = ur[d];
-            du2 += (ur[d] - up) * (ur[d] - up);
+            du2 += (ur[d] - up[d]) * (ur[d] - up[d]);
             u2 += ur[d] * ur[d];
             usnap[(int64_t)d * plane + idx] = ur[d];
         }
