@@ -279,15 +279,22 @@ cudaError_t build_graph(lbm_solver* s, int par) {
 
 namespace blbm {
 
-__global__ void k_finalize(const double* __restrict__ partials, int nparts, double* __restrict__ out) {
+// Grid stage of the FP64 sums: one block of kFinThreads threads adds the
+// per-block partials in a fixed order (thread t takes partials t, t + kFinThreads,
+// ...; then a fixed shuffle tree).  1024 threads keep each thread's chain of
+// FP64 adds short, which matters at GB300's FP64 rate.
+constexpr int kFinThreads = 1024;
+
+__global__ void __launch_bounds__(kFinThreads)
+k_finalize(const double* __restrict__ partials, int nparts, double* __restrict__ out) {
     double v[kNumStats];
 #pragma unroll
     for (int k = 0; k < kNumStats; ++k) v[k] = 0.0;
-    for (int b = threadIdx.x; b < nparts; b += kBlock) {
+    for (int b = threadIdx.x; b < nparts; b += kFinThreads) {
 #pragma unroll
         for (int k = 0; k < kNumStats; ++k) v[k] += partials[(int64_t)b * kNumStats + k];
     }
-    __shared__ double sm[kBlock / 32][kNumStats];
+    __shared__ double sm[kFinThreads / 32][kNumStats];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < kNumStats; ++k)
@@ -297,7 +304,7 @@ __global__ void k_finalize(const double* __restrict__ partials, int nparts, doub
     __syncthreads();
     if (warp == 0) {
         for (int k = 0; k < kNumStats; ++k) {
-            double t = (lane < kBlock / 32) ? sm[lane][k] : 0.0;
+            double t = (lane < kFinThreads / 32) ? sm[lane][k] : 0.0;
             for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
             if (lane == 0) out[k] = t;
         }
@@ -305,7 +312,7 @@ __global__ void k_finalize(const double* __restrict__ partials, int nparts, doub
 }
 
 cudaError_t launch_finalize(const double* partials, int nparts, double* out, cudaStream_t st) {
-    k_finalize<<<1, kBlock, 0, st>>>(partials, nparts, out);
+    k_finalize<<<1, kFinThreads, 0, st>>>(partials, nparts, out);
     return cudaGetLastError();
 }
 
