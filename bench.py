@@ -7,7 +7,8 @@ the yield stress through the Mosolov-Miasnikov duct formula), nu_p = 0.1,
 FP32 population storage, started from rest.  One bench "step" is one lattice
 time step of BOTH Bingham models on their own copy of the duct (PR with
 m = 1e6 and IR), so both fused kernels and the check-step reductions (every
-100 steps) are exercised.  The metric is MLUPS: fluid-cell updates per second.
+100 steps) are exercised.  The metric is MLUPS: fluid-cell updates per second
+(all_cell_mlups counts the solid cells too).
 
 Timing: W untimed warm-up steps, then K timed steps bracketed by a barrier and
 cudaDeviceSynchronize, measured with CUDA events on the solvers' stream (the
@@ -328,6 +329,7 @@ def run_ours(args):
                                            "fluid_cells": nfluid, "autotuned": tuned}),
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "serving": serving,
                 "gpu_launches": 2 * launches_per_model, "clocks": clk,
+                "all_cell_mlups": round(value * mask.size / nfluid, 1),
                 "wall_s_timed_region": round(t1 - t0, 4)}
         print(json.dumps(line), flush=True)
     if ws > 1 and dist.is_initialized():
