@@ -290,6 +290,8 @@ k_finalize(const double* __restrict__ partials, int nparts, double* __restrict__
     double v[kNumStats];
 #pragma unroll
     for (int k = 0; k < kNumStats; ++k) v[k] = 0.0;
+    // unrolled so several partials are in flight; the order of the adds is unchanged
+#pragma unroll 4
     for (int b = threadIdx.x; b < nparts; b += kFinThreads) {
 #pragma unroll
         for (int k = 0; k < kNumStats; ++k) v[k] += partials[(int64_t)b * kNumStats + k];
