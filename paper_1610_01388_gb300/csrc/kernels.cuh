@@ -737,15 +737,20 @@ __device__ __forceinline__ void block_sum_store(V (&v)[kNumStats], double* __res
 // the fused step
 //
 // Minimum resident blocks per SM requested from the register allocator (0 =
-// let it choose).  Tuning knobs, set at build time.
+// let it choose).  PR: 9 blocks of 128 threads (at most 56 registers, 36
+// warps) measured best on GB300 (a tighter cap spills); 256 and 512 threads
+// keep the 64-register cap they reach anyway.  IR (48 registers) is left to
+// the allocator.  BLBM_PR_MINB / BLBM_IR_MINB override at build time.
 #ifndef BLBM_PR_MINB
-#define BLBM_PR_MINB 0
+#define BLBM_PR_MINB -1
 #endif
 #ifndef BLBM_IR_MINB
 #define BLBM_IR_MINB 0
 #endif
-template <int MODEL> constexpr int step_min_blocks() {
-    return MODEL == LBM_MODEL_IR ? BLBM_IR_MINB : BLBM_PR_MINB;
+template <int MODEL, int BLOCK> constexpr int step_min_blocks() {
+    if (MODEL == LBM_MODEL_IR) return BLBM_IR_MINB;
+    if (BLBM_PR_MINB >= 0) return BLBM_PR_MINB;
+    return BLOCK == 128 ? 9 : 1024 / BLOCK;
 }
 
 // One cell of one time step: pull, collide, store; on check steps the cell's
@@ -804,7 +809,7 @@ __device__ __forceinline__ void cell_step(const KParams& kp, const Coef<typename
 // by the tuning table; check steps always run with kBlock so their reduction
 // order does not depend on the tuning.
 template <class L, int MODEL, class S, bool CHECK, int BLOCK = kBlock>
-__global__ void __launch_bounds__(BLOCK, step_min_blocks<MODEL>())
+__global__ void __launch_bounds__(BLOCK, step_min_blocks<MODEL, BLOCK>())
 k_step(const KArgs a, const SrcPlanes<S> src, const DstPlanes<S> dst,
        const uint32_t* __restrict__ links, typename Store<S>::R* __restrict__ tau,
        typename Store<S>::R* __restrict__ usnap, double* __restrict__ partials,
