@@ -338,3 +338,23 @@ def test_two_cells_per_thread(lat, model, block):
             h.close()
     finally:
         lbm.lbm_tuning_clear()
+
+
+@pytest.mark.parametrize("model", ["PR", "IR"])
+def test_porous_sample_1000_steps_fp64(model):
+    """A 64^3 sample of the porous-medium generator (spheres r in [6, 10],
+    porosity 0.7, seed 1), D3Q19, 1000 steps from rest in FP64: the whole
+    velocity field and the flow rate against the oracle at equal step count,
+    and the fluid mass conserved to round-off (walls, periodic box)."""
+    mask, info = W.porous_mask(64, porosity=0.7, r_min=6, r_max=10, seed=1)
+    assert info["reached"]
+    s, o = make_pair("D3Q19", mask, model=model, storage="F64", sigma_y=2e-6, m=1e6,
+                     g=(2e-6, 0, 0), nu_p=0.1, nthreads=0)
+    m0, _ = s.totals()
+    s.step(1000)
+    o.step(1000)
+    assert rel_l2_u(s, o) < 1e-10
+    assert abs(s.flowrate(0) - o.flowrate(0)) < 1e-10 * abs(o.flowrate(0))
+    m1, _ = s.totals()
+    assert abs(m1 - m0) / m0 < 1e-12
+    s.close()

@@ -92,6 +92,10 @@ def test_channel_bingham_ir_plug(bn):
     ex = np.where(ay <= y0, up, g / (2 * nu) * (h * h - YC * YC) - sy / nu * (h - ay))
     assert abs(u.max() - up) / up < 1e-3
     assert np.max(np.abs(u - ex)) / up < 1e-3
+    # mean velocity: U = (g h^2 / 3 nu_p)(1 - 3 xi / 2 + xi^3 / 2), xi = y0 / h
+    xi = y0 / h
+    ubar = g * h * h / (3 * nu) * (1 - 1.5 * xi + 0.5 * xi ** 3)
+    assert abs(u.mean() - ubar) / ubar < 2e-3
     # the plug is flat: rows inside the yield half-width share one speed
     inside = ay < y0 - 1.0
     if inside.sum() > 1:
