@@ -311,6 +311,7 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
 
     e2e = run_e2e(args, mask, nfluid, g, sy, dev)
+    steady = run_steady(args, mask, nfluid, g, sy) if args.steady else None
     serving = None
     if args.serve_requests > 0:
         serving = {"form": "served FP16-offset storage (stochastic rounding) vs FP32, batched",
@@ -328,12 +329,40 @@ def run_ours(args):
                 "config": workload_config({"per_rank": "independent duct pair per GPU",
                                            "fluid_cells": nfluid, "autotuned": tuned}),
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "serving": serving,
+                "time_to_steady": steady,
                 "gpu_launches": 2 * launches_per_model, "clocks": clk,
                 "all_cell_mlups": round(value * mask.size / nfluid, 1),
                 "wall_s_timed_region": round(t1 - t0, 4)}
         print(json.dumps(line), flush=True)
     if ws > 1 and dist.is_initialized():
         dist.destroy_process_group()
+
+
+def run_steady(args, mask, nfluid, g, sy):
+    """Time to steady state of the start-up flow (both models, from rest):
+    check every 1000 steps, steady when the residual between consecutive
+    checks, sqrt(sum |u - u_prev|^2 / sum |u|^2), falls below the tolerance."""
+    import torch
+    from paper_1610_01388_gb300 import lbm
+    out = {"tolerance": args.steady_tol, "check_every": 1000, "step_cap": args.steady_cap}
+    for model in ("IR", "PR"):
+        s = lbm.Solver(LATTICE, mask, model=model, storage=STORAGE, mu_p=NU_P, sigma_y=sy,
+                       m=M_PR, g=(g, 0.0, 0.0), check_every=1000, use_torch=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        steps, r = 0, -1.0
+        while steps < args.steady_cap:
+            s.step(1000)
+            steps += 1000
+            r, _, _ = s.residual()
+            if 0.0 <= r < args.steady_tol:
+                break
+        dt = time.perf_counter() - t0
+        out[model] = {"steps": steps, "seconds": round(dt, 3), "residual": r,
+                      "steady": bool(0.0 <= r < args.steady_tol),
+                      "flow_rate_x": s.flowrate(0), "mlups": round(nfluid * steps / dt / 1e6, 1)}
+        s.close()
+    return out
 
 
 def run_e2e(args, mask, nfluid, g, sy, dev):
@@ -529,6 +558,10 @@ def main(argv=None):
     ap.add_argument("--lattice", default=LATTICE, choices=["D3Q15", "D3Q19", "D3Q27"])
     ap.add_argument("--storage", default=STORAGE, choices=["F32", "F64", "F16", "BF16"])
     ap.add_argument("--nz", type=int, default=NZ)
+    ap.add_argument("--steady", action="store_true",
+                    help="also run both models from rest to steady state and report the time")
+    ap.add_argument("--steady-tol", type=float, default=1e-6)
+    ap.add_argument("--steady-cap", type=int, default=2_000_000)
     args = ap.parse_args(argv)
     NX, NY, NZ = args.nx, args.ny, args.nz
     LATTICE, STORAGE = args.lattice, args.storage
