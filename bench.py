@@ -85,16 +85,22 @@ NCU_TRAFFIC = {
     ("F16", "PR", 128, 1): 451421253, ("F16", "PR", 256, 1): 450409649, ("F16", "PR", 512, 1): 450565114,
     ("F16", "PR", 128, 2): 450177867, ("F16", "PR", 256, 2): 450250403,
 }
-KERNEL_FINGERPRINT = "d42a49837e05f8e8"
+KERNEL_FINGERPRINT = "d5844a4616f78015"
 KERNEL_SOURCES = ("kernels.cuh", "lattice.cuh", "lbm_internal.h", "fastdiv.h", "kern_d3q27.cu")
 
 
 def kernel_fingerprint():
+    """SHA-256 of the device-code sources without comments and blank space
+    (a comment edit does not change what was captured)."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for name in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, "paper_1610_01388_gb300", "csrc", name), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1610_01388_gb300", "csrc", name)) as fh:
+            src = fh.read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        h.update(" ".join(src.split()).encode())
     return h.hexdigest()[:16]
 
 

@@ -1,6 +1,7 @@
 // Fused pull stream-and-collide kernels for the PR and IR Bingham models.
 //
-// One thread owns one cell.  Per fluid cell and time step it
+// One thread owns one cell (k_step; k_step2 runs two cells per thread with
+// the collision in packed two-wide FP32).  Per fluid cell and time step it
 //   1. gathers the Q incoming populations (eq. 8, pull form): population i
 //      comes from the cell at x - c_i (periodic wrap) or, when that cell is
 //      solid, is the cell's own outgoing population in the opposite direction
@@ -10,8 +11,9 @@
 //      PR  T = Pi - rho c_s^2 I - rho u u, D = -T/(2 tau_old c_s^2)
 //          (eq. LBM_strain_rate), gdot = sqrt(2 D:D), nu_app from eqs.
 //          (Pap_reg_1)/(PR_interpolation), tau = 1/2 + nu_app/c_s^2
-//          (eq. tau_visc), TRT with tau_odd from Lambda (Sec. 2.1) and the
-//          exact-difference force of eq. (14);
+//          (eq. tau_visc), or the Newton-implicit tau of Sec. 3; TRT with
+//          tau_odd from Lambda (Sec. 2.1) and the exact-difference force of
+//          eq. (14);
 //      IR  u = (j + F/2)/rho, T as above, the closed-form solution of
 //          eq. (Vikh_main_short) (eqs. Vikh_sigmaS_formula/tensor, yield where
 //          |T| >= sqrt2 sigma_y), A = -sigma_bar + s/2, and the post-collision
@@ -19,10 +21,11 @@
 //          eqs. (Vikh_postCol)/(Vikh_f_stress)/(Vikh_force);
 //   4. stores the Q outgoing populations (and, PR, the new tau in place).
 //
-// Populations are stored as offsets f_i - w_i from the rest state, so every
-// moment is formed from small numbers (no cancellation against the weights).
-// On check steps the same launch also accumulates the flow-rate sums and the
-// residual against the previous snapshot into per-block FP64 partials.
+// Populations are stored as offsets f_i - w_i from the rest state (scaled per
+// direction for the 16-bit forms), so every moment is formed from small
+// numbers (no cancellation against the weights).  On check steps the same
+// launch also accumulates the flow-rate sums and the residual against the
+// previous snapshot into per-block partials, summed in FP64 in a fixed order.
 #pragma once
 
 #include <cstdint>
