@@ -265,10 +265,10 @@ template <> struct Store<__half> {
     }
     // populations i and its opposite (same weight) in one conversion
     template <class L, int i>
-    static __device__ __forceinline__ void st2(__half* pi, __half* po, R vi, R vo, uint32_t rnd) {
-        const uint32_t d = cvt_rs_f16x2(vi, vo, rnd);
-        st_u16(pi, d >> 16);
-        st_u16(po, d);
+    // pi and po = pi + 1 are the two halves of one 4-byte-aligned word (the
+    // interleaved pair layout): f_i in the low half, f_o in the high half
+    static __device__ __forceinline__ void st2(__half* pi, __half*, R vi, R vo, uint32_t rnd) {
+        *reinterpret_cast<uint32_t*>(pi) = cvt_rs_f16x2(vo, vi, rnd);
     }
     static __device__ __forceinline__ __half enc(double off, double w) { return __double2half(off / w * kScale); }
     static __device__ __forceinline__ double dec(__half v, double w) { return (double)__half2float(v) * (w / kScale); }
@@ -286,11 +286,9 @@ template <> struct Store<__nv_bfloat16> {
         st_u16(p, cvt_rs_bf16x2(v, 0.0f, rnd) >> 16);
     }
     template <class L, int i>
-    static __device__ __forceinline__ void st2(__nv_bfloat16* pi, __nv_bfloat16* po, R vi, R vo,
+    static __device__ __forceinline__ void st2(__nv_bfloat16* pi, __nv_bfloat16*, R vi, R vo,
                                                uint32_t rnd) {
-        const uint32_t d = cvt_rs_bf16x2(vi, vo, rnd);
-        st_u16(pi, d >> 16);
-        st_u16(po, d);
+        *reinterpret_cast<uint32_t*>(pi) = cvt_rs_bf16x2(vo, vi, rnd);
     }
     static __device__ __forceinline__ __nv_bfloat16 enc(double off, double w) { return __double2bfloat16(off / w); }
     static __device__ __forceinline__ double dec(__nv_bfloat16 v, double w) { return (double)__bfloat162float(v) * w; }
@@ -321,26 +319,48 @@ template <> __device__ __forceinline__ const Coef<double>& coef<double>(const KA
 
 // Base pointer of every population plane, passed by value in the kernel
 // parameters: an address is then one multiply-add of the 32-bit cell index.
+// Population layout.  FP32 / FP64: plane i holds population i of every cell.
+// 16-bit forms: the rest population has plane 0; an opposite pair (i, i + 1),
+// i odd, shares planes i and i + 1 as one plane of 32-bit words holding f_i
+// in the low and f_{i+1} in the high half of cell n's word, so the pair's
+// packed stochastic-rounding result is one aligned 32-bit store.  Element
+// (i, n) is at pop_base(i) + pop_step(i) n; the total is Q planes either way.
+template <class S> __host__ __device__ constexpr bool pairs_interleaved() { return sizeof(S) == 2; }
+template <class S> __host__ __device__ constexpr int64_t pop_base(int i, int64_t plane) {
+    return (!pairs_interleaved<S>() || i == 0) ? i * plane : (i - ((i - 1) & 1)) * plane + ((i - 1) & 1);
+}
+template <class S> __host__ __device__ constexpr int pop_step(int i) {
+    return (pairs_interleaved<S>() && i > 0) ? 2 : 1;
+}
+
 template <class S> struct SrcPlanes {
-    const S* p[27];
-    template <int i> __device__ __forceinline__ const S* at(int n) const { return p[i] + n; }
+    const S* p[27];   // p[i] = buffer + pop_base(i)
+    template <int i> __device__ __forceinline__ const S* at(int n) const {
+        return p[i] + (int64_t)pop_step<S>(i) * n;
+    }
 };
 template <class S> struct DstPlanes {
     S* p[27];
-    template <int i> __device__ __forceinline__ S* at(int n) const { return p[i] + n; }
+    template <int i> __device__ __forceinline__ S* at(int n) const {
+        return p[i] + (int64_t)pop_step<S>(i) * n;
+    }
 };
 // Planes of one buffer addressed by a stride (batched launches, where the
-// pointers differ per domain): element i * plane + n, in 32-bit arithmetic
-// (the batch admits only domains with Q * plane < 2^31).
+// pointers differ per domain), in 32-bit arithmetic (the batch admits only
+// domains with Q * plane < 2^31, and every element index is below that).
 template <class S> struct SrcStride {
     const S* base;
     int plane;
-    template <int i> __device__ __forceinline__ const S* at(int n) const { return base + (i * plane + n); }
+    template <int i> __device__ __forceinline__ const S* at(int n) const {
+        return base + ((int)pop_base<S>(i, plane) + pop_step<S>(i) * n);
+    }
 };
 template <class S> struct DstStride {
     S* base;
     int plane;
-    template <int i> __device__ __forceinline__ S* at(int n) const { return base + (i * plane + n); }
+    template <int i> __device__ __forceinline__ S* at(int n) const {
+        return base + ((int)pop_base<S>(i, plane) + pop_step<S>(i) * n);
+    }
 };
 
 // cell index -> (x, y, z)
@@ -1104,7 +1124,7 @@ k_convert(const KParams kp, int q, bool to_device, S* __restrict__ f, double* __
 #pragma unroll
     for (int i = 0; i < L::Q; ++i)
         if (i == q) w = L::w(i);
-    S* p = f + (int64_t)q * kp.plane + idx;
+    S* p = f + pop_base<S>(q, kp.plane) + (int64_t)pop_step<S>(q) * idx;
     if (to_device)
         *p = Store<S>::enc(buf[idx] - w, w);
     else
@@ -1121,7 +1141,8 @@ k_gather_cells(const KParams kp, const S* __restrict__ f, const int64_t* __restr
     const int64_t c = cells[k];
     static_for<0, L::Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
-        out[(int64_t)i * n + k] = Store<S>::dec(f[(int64_t)i * kp.plane + c], L::w(i)) + L::w(i);
+        out[(int64_t)i * n + k] =
+            Store<S>::dec(f[pop_base<S>(i, kp.plane) + (int64_t)pop_step<S>(i) * c], L::w(i)) + L::w(i);
     });
 }
 
@@ -1184,12 +1205,12 @@ template <class R> inline Coef<R> make_coef_lat(const KParams& kp, int lat) {
 
 template <class L, class S> inline SrcPlanes<S> src_planes(const void* f, int64_t plane) {
     SrcPlanes<S> P{};
-    for (int i = 0; i < L::Q; ++i) P.p[i] = (const S*)f + (int64_t)i * plane;
+    for (int i = 0; i < L::Q; ++i) P.p[i] = (const S*)f + pop_base<S>(i, plane);
     return P;
 }
 template <class L, class S> inline DstPlanes<S> dst_planes(void* f, int64_t plane) {
     DstPlanes<S> P{};
-    for (int i = 0; i < L::Q; ++i) P.p[i] = (S*)f + (int64_t)i * plane;
+    for (int i = 0; i < L::Q; ++i) P.p[i] = (S*)f + pop_base<S>(i, plane);
     return P;
 }
 
