@@ -1008,8 +1008,16 @@ __device__ __forceinline__ void batch_tile(const BatchDesc& D, int tile, int pha
 // t + gridDim.x, ...).  With one CTA per tile this is the plain launch; with
 // fewer CTAs it is a persistent grid.  Partials are indexed by tile, so check
 // steps reduce in the same order for every grid size.
+// Register budget of the batch kernel: plain PR steps of the 16-bit forms
+// keep 4 resident blocks (64 registers; the interleaved pair addressing
+// otherwise takes 72 and 3 blocks).  Everything else is left to the
+// allocator (FP32 and FP64 fit without it; a budget would spill there).
+template <int MODEL, class S, bool CHECK> constexpr int batch_min_blocks() {
+    return (MODEL != LBM_MODEL_IR && !CHECK && sizeof(S) == 2) ? 4 : 0;
+}
+
 template <class L, int MODEL, class S, bool CHECK>
-__global__ void __launch_bounds__(kBlock)
+__global__ void __launch_bounds__(kBlock, batch_min_blocks<MODEL, S, CHECK>())
 k_step_batch(const BatchDesc* __restrict__ descs, const int* __restrict__ block_dom, int ntiles,
              int phase, double* __restrict__ partials) {
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
