@@ -425,7 +425,9 @@ template <class R> struct Mom {
 // 0; c_y = +-1; c_z = +-1; sign of c_x c_y, c_x c_z, c_y c_z) and the moments
 // are sums and differences of those class sums.  Each class sum starts as its
 // first member (no add to a zero).  f is in memory units; beta_i turns each
-// value into an offset (a multiply, left out where beta_i = 1).
+// value into an offset.  Where beta_i != 1 it is applied inside each class
+// sum's multiply-add (one instruction per class membership, no separate
+// multiply per population).
 enum { kXp, kXm, kX0, kYp, kYm, kZp, kZm, kPxy, kMxy, kPxz, kMxz, kPyz, kMyz, kNumClasses };
 
 __host__ __device__ constexpr bool in_class(int k, int cx, int cy, int cz) {
@@ -448,14 +450,16 @@ __device__ __forceinline__ Mom<R> moments(const R (&f)[L::Q]) {
         constexpr int i = decltype(I)::value;
         constexpr int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
         constexpr auto beta = Store<S>::template beta<L, i>();
-        R v;
-        if constexpr (beta == 1) v = f[i];
-        else v = f[i] * R(beta);
         static_for<0, kNumClasses>([&](auto K) {
             constexpr int k = decltype(K)::value;
             if constexpr (in_class(k, cx, cy, cz)) {
-                if constexpr (first_in_class<L>(k) == i) acc[k] = v;
-                else acc[k] += v;
+                if constexpr (beta == 1) {
+                    if constexpr (first_in_class<L>(k) == i) acc[k] = f[i];
+                    else acc[k] += f[i];
+                } else {
+                    if constexpr (first_in_class<L>(k) == i) acc[k] = R(f[i] * R(beta));
+                    else acc[k] = acc[k] + f[i] * R(beta);
+                }
             }
         });
     });
@@ -760,18 +764,20 @@ __device__ __forceinline__ void block_sum_store(V (&v)[kNumStats], double* __res
 // the fused step
 //
 // Minimum resident blocks per SM requested from the register allocator (0 =
-// let it choose).  PR: 9 blocks of 128 threads (at most 56 registers, 36
-// warps) measured best on GB300 (a tighter cap spills); 256 and 512 threads
-// keep the 64-register cap they reach anyway.  IR (48 registers) is left to
-// the allocator.  BLBM_PR_MINB / BLBM_IR_MINB override at build time.
+// let it choose).  PR in FP32 arithmetic: 9 blocks of 128 threads (at most 56
+// registers, 36 warps) measured best on GB300 (a tighter cap spills); 256 and
+// 512 threads keep the 64-register cap they reach anyway.  IR (48 registers)
+// and FP64 arithmetic (which these caps would make spill) are left to the
+// allocator.  BLBM_PR_MINB / BLBM_IR_MINB override at build time.
 #ifndef BLBM_PR_MINB
 #define BLBM_PR_MINB -1
 #endif
 #ifndef BLBM_IR_MINB
 #define BLBM_IR_MINB 0
 #endif
-template <int MODEL, int BLOCK> constexpr int step_min_blocks() {
+template <int MODEL, class S, int BLOCK> constexpr int step_min_blocks() {
     if (MODEL == LBM_MODEL_IR) return BLBM_IR_MINB;
+    if (std::is_same<typename Store<S>::R, double>::value) return 0;
     if (BLBM_PR_MINB >= 0) return BLBM_PR_MINB;
     return BLOCK == 128 ? 9 : 1024 / BLOCK;
 }
@@ -832,7 +838,7 @@ __device__ __forceinline__ void cell_step(const KParams& kp, const Coef<typename
 // by the tuning table; check steps always run with kBlock so their reduction
 // order does not depend on the tuning.
 template <class L, int MODEL, class S, bool CHECK, int BLOCK = kBlock>
-__global__ void __launch_bounds__(BLOCK, step_min_blocks<MODEL, BLOCK>())
+__global__ void __launch_bounds__(BLOCK, step_min_blocks<MODEL, S, BLOCK>())
 k_step(const KArgs a, const SrcPlanes<S> src, const DstPlanes<S> dst,
        const uint32_t* __restrict__ links, typename Store<S>::R* __restrict__ tau,
        typename Store<S>::R* __restrict__ usnap, double* __restrict__ partials,
