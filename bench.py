@@ -323,9 +323,8 @@ def run_ours(args):
         serving = {"form": "served FP16-offset storage (stochastic rounding) vs FP32, batched",
                    "budget_gb": 120, "rate_per_s": args.serve_rate,
                    "tolerance": args.serve_tolerance, "step_cap": args.serve_max_steps,
-                   "mix": "D2Q9 channels 4 x (17..257), D3Q19/D3Q27 ducts 64 x (33..97)^2, "
-                          "D3Q19/D3Q27 porous boxes (32..64)^3 porosity 0.7; Bn U[0.1,10]; PR/IR",
-                   "runs": [run_serving(args, st) for st in ("F16", "F32")]}
+                   "mix": SERVE_MIX_FULL if args.serve_full else SERVE_MIX,
+                   "runs": [run_serving(args, st) for st in args.serve_storage.split(",")]}
     cpu = run_cpu_baseline(args) if (rank == 0 and ws == 1 and not args.no_cpu) else None
     if rank == 0:
         line = {"metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": ws,
@@ -406,6 +405,20 @@ def run_e2e(args, mask, nfluid, g, sy, dev):
 
 # --- serving ----------------------------------------------------------------------
 
+SERVE_MIX = ("D2Q9 channels 4 x (17..257), D3Q19/D3Q27 ducts 64 x (33..97)^2, "
+             "D3Q19/D3Q27 porous boxes (32..64)^3 porosity 0.7 radius 4-6; Bn U[0.1,10]; PR/IR")
+SERVE_MIX_FULL = ("D2Q9 channels 4 x (17..257), D3Q19/D3Q27 ducts 64 x (33..193)^2, "
+                  "D3Q19/D3Q27 porous boxes (64..256)^3 (sides in steps of 16, 2 seeded "
+                  "geometries per side) porosity 0.7 radius 6-10; Bn U[0.1,10]; PR/IR")
+
+
+def _serve_sizes(args):
+    if args.serve_full:
+        return dict(duct_sides=(32, 192), porous_sides=(64, 256), porous_radius=(6.0, 10.0),
+                    porous_pool=2)
+    return {}
+
+
 def run_serving(args, storage):
     """A Poisson stream of independent solves (channels, ducts, porous boxes;
     Bn uniform in [0.1, 10]; PR or IR) through the continuous-batching server
@@ -417,7 +430,7 @@ def run_serving(args, storage):
     from paper_1610_01388_gb300 import workloads as W
     reqs = W.serving_requests(n=args.serve_requests, rate=args.serve_rate, seed=7,
                               storage=storage, max_steps=args.serve_max_steps,
-                              tolerance=args.serve_tolerance)
+                              tolerance=args.serve_tolerance, **_serve_sizes(args))
     schedule = None
     if not args.no_tune:
         # the batch schedule, tuned on a mix drawn from the same generator
@@ -425,7 +438,7 @@ def run_serving(args, storage):
         from paper_1610_01388_gb300 import autotune
         sample = W.serving_requests(n=48, rate=args.serve_rate, seed=8, storage=storage,
                                     max_steps=args.serve_max_steps,
-                                    tolerance=args.serve_tolerance)
+                                    tolerance=args.serve_tolerance, **_serve_sizes(args))
         mix = [(r["lattice"], r["mask"], dict(model=r["model"], storage=r["storage"],
                                               mu_p=r["mu_p"], sigma_y=r["sigma_y"], m=r["m"],
                                               g=r["g"])) for r in sample]
@@ -557,6 +570,11 @@ def main(argv=None):
     ap.add_argument("--serve-rate", type=float, default=150.0, help="Poisson arrival rate, 1/s")
     ap.add_argument("--serve-max-steps", type=int, default=3000)
     ap.add_argument("--serve-tolerance", type=float, default=1e-3)
+    ap.add_argument("--serve-storage", default="F16,F32",
+                    help="storage forms served, comma-separated, in order")
+    ap.add_argument("--serve-full", action="store_true",
+                    help="serve the full-size mix (ducts to 192^2, porous boxes to 256^3) "
+                         "instead of the scaled-down one")
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu dram bytes per launch of the dominant kernel, if captured")
     ap.add_argument("--nx", type=int, default=NX, help="duct length (other workloads)")
@@ -573,6 +591,8 @@ def main(argv=None):
     LATTICE, STORAGE = args.lattice, args.storage
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if not set(args.serve_storage.split(",")) <= {"F32", "F64", "F16", "BF16"}:
+        ap.error("--serve-storage takes F32, F64, F16, BF16, comma-separated")
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -250,14 +250,32 @@ def porous_params(nu_p: float = 0.1, d_mean: float = 16.0, g: float = 2e-5, bn: 
     return {"g": g, "sigma_y": bn * g * d_mean / 4.0, "nu_p": nu_p}
 
 
+_POROUS_POOL: dict = {}
+
+
+def _pooled_porous(side: int, seed: int, r_min: float, r_max: float):
+    key = (side, seed, r_min, r_max)
+    if key not in _POROUS_POOL:
+        _POROUS_POOL[key] = porous_mask(side, porosity=0.7, r_min=r_min, r_max=r_max, seed=seed)[0]
+    return _POROUS_POOL[key]
+
+
 def serving_requests(n: int = 200, rate: float = 40.0, seed: int = 7, storage: str = "F16",
                      channel_widths=(16, 256), duct_sides=(32, 96), duct_length: int = 64,
-                     porous_sides=(32, 64), max_steps: int = 2000, tolerance: float = 1e-4):
+                     porous_sides=(32, 64), max_steps: int = 2000, tolerance: float = 1e-4,
+                     porous_radius=(4.0, 6.0), porous_pool: int = 0):
     """Poisson stream of independent solves: 2D channels (D2Q9, 4 x width),
     square ducts (D3Q19/D3Q27, side x side x length) and porous boxes
-    (D3Q19/D3Q27, random spheres, porosity 0.7), Bingham number uniform in
-    [0.1, 10], model PR or IR with equal probability.  Returns a list of dicts
-    with the arrival time (s) and everything a solver needs."""
+    (D3Q19/D3Q27, random spheres of radius U[porous_radius], porosity 0.7),
+    Bingham number uniform in [0.1, 10], model PR or IR with equal
+    probability.  Returns a list of dicts with the arrival time (s) and
+    everything a solver needs.
+
+    porous_pool = 0 draws a fresh geometry per porous request.  porous_pool =
+    P > 0 rounds each box side to a multiple of 16 and draws its geometry from
+    P seeds per side, generated once per process (a 256^3 box takes seconds
+    on the host, which a stream of thousands of requests cannot pay each
+    time); Bingham number and model are still drawn per request."""
     rng = np.random.Generator(np.random.PCG64(seed))
     t = 0.0
     out = []
@@ -278,7 +296,12 @@ def serving_requests(n: int = 200, rate: float = 40.0, seed: int = 7, storage: s
             lat, g = ("D3Q19" if rng.integers(2) == 0 else "D3Q27"), (p["g"], 0.0, 0.0)
         else:
             s = int(rng.integers(porous_sides[0], porous_sides[1] + 1))
-            mask, _ = porous_mask(s, porosity=0.7, r_min=4, r_max=6, seed=int(rng.integers(1 << 30)))
+            if porous_pool > 0:
+                s = min(max(16 * round(s / 16), porous_sides[0]), porous_sides[1])
+                mask = _pooled_porous(s, int(rng.integers(porous_pool)) + 1, *porous_radius)
+            else:
+                mask, _ = porous_mask(s, porosity=0.7, r_min=porous_radius[0],
+                                      r_max=porous_radius[1], seed=int(rng.integers(1 << 30)))
             p = porous_params(nu_p=0.1, d_mean=10.0, g=2e-5, bn=bn)
             lat, g = ("D3Q19" if rng.integers(2) == 0 else "D3Q27"), (p["g"], 0.0, 0.0)
         out.append({"arrival": t, "lattice": lat, "mask": mask, "model": model,

@@ -36,3 +36,34 @@ def test_permutation_maps_velocity_orders():
     c2 = np.array([[-1, 0, 0], [0, 0, 0], [1, 0, 0]])
     p = W.permutation(c1, c2)
     assert np.array_equal(c2[p], c1)
+
+
+def test_serving_stream_is_seeded_and_in_range():
+    a = W.serving_requests(n=40, rate=50.0, seed=11, duct_sides=(32, 48), porous_sides=(32, 40))
+    b = W.serving_requests(n=40, rate=50.0, seed=11, duct_sides=(32, 48), porous_sides=(32, 40))
+    assert [r["arrival"] for r in a] == [r["arrival"] for r in b]
+    assert all(np.array_equal(x["mask"], y["mask"]) for x, y in zip(a, b))
+    t = [r["arrival"] for r in a]
+    assert all(t1 > t0 for t0, t1 in zip(t, t[1:]))
+    for r in a:
+        assert 0.1 <= r["bn"] <= 10.0 and r["model"] in ("PR", "IR")
+        if r["kind"] == "channel":
+            assert r["lattice"] == "D2Q9" and 17 <= r["mask"].shape[1] <= 257
+        elif r["kind"] == "duct":
+            assert r["lattice"] in ("D3Q19", "D3Q27") and 33 <= r["mask"].shape[1] <= 49
+        else:
+            assert r["lattice"] in ("D3Q19", "D3Q27") and 32 <= r["mask"].shape[0] <= 40
+
+
+def test_serving_stream_pools_porous_geometry():
+    reqs = W.serving_requests(n=60, rate=50.0, seed=5, porous_sides=(32, 64), porous_pool=2)
+    porous = [r for r in reqs if r["kind"] == "porous"]
+    assert porous
+    shapes = {r["mask"].shape[0] for r in porous}
+    assert all(s % 16 == 0 and 32 <= s <= 64 for s in shapes)
+    # at most pool-size distinct geometries per side, each generated once
+    for s in shapes:
+        ids = {id(r["mask"]) for r in porous if r["mask"].shape[0] == s}
+        assert 1 <= len(ids) <= 2
+    # the Bingham number and model are still drawn per request
+    assert len({r["bn"] for r in porous}) == len(porous)
