@@ -373,6 +373,9 @@ __device__ __forceinline__ void cell_xyz(const KParams& kp, int idx, int& x, int
 
 // ---------------------------------------------------------------------------
 // streaming (pull) with halfway bounce-back
+#ifndef BLBM_WARP_UNIFORM_GATHER
+#define BLBM_WARP_UNIFORM_GATHER 1
+#endif
 template <class L, class S, class Src>
 __device__ __forceinline__ void gather(const KParams& kp, const Src& P, uint32_t lk,
                                        int idx, typename Store<S>::R (&v)[L::Q]) {
@@ -399,7 +402,17 @@ __device__ __forceinline__ void gather(const KParams& kp, const Src& P, uint32_t
         if constexpr (cz < 0) off += dzp;
         return off;
     };
-    if (lk == 0u) {
+    // The path is chosen per warp: a warp takes the plain pull only when none
+    // of its cells has a solid neighbour.  A per-thread choice makes a warp
+    // that mixes wall and interior cells run both paths one after the other,
+    // which is most warps in a porous medium; the select path is exact for
+    // interior cells too (their link bits are 0).
+#if BLBM_WARP_UNIFORM_GATHER
+    const bool plain = __all_sync(__activemask(), lk == 0u);
+#else
+    const bool plain = lk == 0u;
+#endif
+    if (plain) {
         // no solid neighbour: plain pull, no per-population selects
         static_for<0, L::Q>([&](auto I) {
             constexpr int i = decltype(I)::value;
@@ -1014,12 +1027,24 @@ __device__ __forceinline__ void batch_tile(const BatchDesc& D, int tile, int pha
 // t + gridDim.x, ...).  With one CTA per tile this is the plain launch; with
 // fewer CTAs it is a persistent grid.  Partials are indexed by tile, so check
 // steps reduce in the same order for every grid size.
-// Register budget of the batch kernel: plain PR steps of the 16-bit forms
-// keep 4 resident blocks (64 registers; the interleaved pair addressing
-// otherwise takes 72 and 3 blocks).  Everything else is left to the
-// allocator (FP32 and FP64 fit without it; a budget would spill there).
+// Register budget of the batch kernel: plain PR steps in FP32 arithmetic keep
+// 4 resident 256-thread blocks (64 registers).  Without it the 16-bit forms
+// take 72 registers and FP32 storage 70 (the descriptor's coefficients are
+// loaded, not kernel-parameter operands), leaving 3 blocks; on a single
+// D3Q27 duct the FP32 PR batch step measured 170 us without and 154 us with
+// the budget.  IR, check steps and FP64 are left to the allocator.
+// BLBM_BATCH_PR_MINB (16-bit) / BLBM_BATCH_PR32_MINB (FP32) override at build
+// time.
+#ifndef BLBM_BATCH_PR_MINB
+#define BLBM_BATCH_PR_MINB 4
+#endif
+#ifndef BLBM_BATCH_PR32_MINB
+#define BLBM_BATCH_PR32_MINB 4
+#endif
 template <int MODEL, class S, bool CHECK> constexpr int batch_min_blocks() {
-    return (MODEL != LBM_MODEL_IR && !CHECK && sizeof(S) == 2) ? 4 : 0;
+    return (MODEL == LBM_MODEL_IR || CHECK) ? 0
+         : sizeof(S) == 2 ? BLBM_BATCH_PR_MINB
+         : sizeof(S) == 4 ? BLBM_BATCH_PR32_MINB : 0;
 }
 
 template <class L, int MODEL, class S, bool CHECK>
