@@ -48,26 +48,48 @@ BN = 2.0
 M_PR = 1e6
 CHECK_EVERY = 100
 SAMPLE_NX = 4          # x-extent of the oracle's sample of the duct (periodic along x)
+POROUS = 0             # > 0: a porous box of this side replaces the duct
 
 
 def workload_params():
     from paper_1610_01388_gb300 import workloads as W
+    if POROUS:
+        prm = W.porous_params(nu_p=NU_P, d_mean=16.0, g=2e-5, bn=BN)
+        return prm["g"], prm["sigma_y"]
     prm = W.duct_params(H=NY - 1, nu_p=NU_P, u_newton=0.02, bn=BN)
     return prm["g"], prm["sigma_y"]
 
 
 def workload_config(extra=None):
+    q = {"D3Q15": 15, "D3Q19": 19}.get(LATTICE, 27)
+    pop_mb = 2 * q * NX * NY * NZ * {"F64": 8, "F32": 4}.get(STORAGE, 2) / 1e6
     cfg = {"workload": f"square duct {LATTICE} {NX}x{NY}x{NZ} ({NY - 1}x{NZ - 1} fluid "
                        "cross-section), "
                        f"PR (m={M_PR:g}) + IR per step, Bn={BN:g}, nu_p={NU_P}, {STORAGE} populations, "
                        f"check step every {CHECK_EVERY}",
            "lattice": LATTICE, "nx": NX, "ny": NY, "nz": NZ, "models": ["PR", "IR"],
            "storage": STORAGE,
-           "l2": "inputs larger than L2 (populations per model: "
-                 f"{2 * (19 if LATTICE == 'D3Q19' else 27) * NX * NY * NZ * {'F64': 8, 'F32': 4}.get(STORAGE, 2) / 1e6:.0f} MB)"}
+           "l2": f"inputs {'larger' if pop_mb > 129 else 'smaller'} than L2 (populations per model: "
+                 f"{pop_mb:.0f} MB)"}
+    if POROUS:
+        cfg.update({"workload": f"porous box {LATTICE} {POROUS}^3 (random non-overlapping spheres, "
+                                "radius 6-10, porosity 0.7, seed 1), "
+                                f"PR (m={M_PR:g}) + IR per step, Bn={BN:g}, nu_p={NU_P}, "
+                                f"{STORAGE} populations, check step every {CHECK_EVERY}",
+                    "nx": POROUS, "ny": POROUS, "nz": POROUS})
     if extra:
         cfg.update(extra)
     return cfg
+
+
+def workload_mask(nx=None):
+    """The bench's geometry: the square duct, or the porous box of --porous
+    (its first nx x-layers when nx is given)."""
+    from paper_1610_01388_gb300 import workloads as W
+    if POROUS:
+        m = W.porous_mask(POROUS, porosity=0.7, r_min=6.0, r_max=10.0, seed=1)[0]
+        return np.ascontiguousarray(m[:, :, :nx]) if nx else m
+    return W.duct_mask(nx or NX, NY, NZ)
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
@@ -109,7 +131,7 @@ def ncu_traffic(storage, model, block, cpt, override=None):
         return override
     if KERNEL_FINGERPRINT is None or kernel_fingerprint() != KERNEL_FINGERPRINT:
         return None
-    if (LATTICE, NX, NY, NZ) != ("D3Q27", 256, 128, 128):
+    if POROUS or (LATTICE, NX, NY, NZ) != ("D3Q27", 256, 128, 128):
         return None
     return NCU_TRAFFIC.get((storage, model, block, cpt))
 
@@ -235,7 +257,7 @@ def run_ours(args):
         _build.build()
     dev = torch.device("cuda", local)
     g, sy = workload_params()
-    mask = W.duct_mask(NX, NY, NZ)
+    mask = workload_mask()
     nfluid = int((mask == 0).sum())
 
     # the project's autotuner picks the step kernel's block size for this
@@ -497,7 +519,7 @@ def _oracle_states():
     import oracle
     from paper_1610_01388_gb300 import workloads as W
     g, sy = workload_params()
-    mask = W.duct_mask(SAMPLE_NX, NY, NZ)
+    mask = workload_mask(SAMPLE_NX)
     states = []
     for model in ("IR", "PR"):
         p = oracle.params(model=model, nu_p=NU_P, sigma_y=sy, m=M_PR, g=(g, 0, 0))
@@ -522,7 +544,7 @@ def run_cpu_baseline(args):
     dt = time.perf_counter() - t0
     return {"value": round(2.0 * nf * n / dt / 1e6, 4), "unit": "MLUPS",
             "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"{SAMPLE_NX}x{NY}x{NZ} slab of the duct (both models, {nf} fluid cells "
+            "sample": f"{SAMPLE_NX}x{NY}x{NZ} slab of the {'porous box' if POROUS else 'duct'} (both models, {nf} fluid cells "
                       f"each), {n} steps in {dt:.1f} s, FP64"}
 
 
@@ -547,7 +569,7 @@ def run_reference(args):
             "config": workload_config({"sample": f"{SAMPLE_NX}x{NY}x{NZ} slab per step"}),
             "cpu_baseline": {"value": round(value, 4), "unit": "MLUPS",
                              "cores": oracle.num_threads(), "kind": "oracle",
-                             "sample": f"{SAMPLE_NX}x{NY}x{NZ} slab of the duct, both models, "
+                             "sample": f"{SAMPLE_NX}x{NY}x{NZ} slab of the {'porous box' if POROUS else 'duct'}, both models, "
                                        "one time step each per bench step"},
             "e2e": {"value": round(value, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -555,7 +577,7 @@ def run_reference(args):
 
 
 def main(argv=None):
-    global NX, NY, NZ, LATTICE, STORAGE
+    global NX, NY, NZ, LATTICE, STORAGE, POROUS
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2000)
@@ -582,6 +604,9 @@ def main(argv=None):
     ap.add_argument("--lattice", default=LATTICE, choices=["D3Q15", "D3Q19", "D3Q27"])
     ap.add_argument("--storage", default=STORAGE, choices=["F32", "F64", "F16", "BF16"])
     ap.add_argument("--nz", type=int, default=NZ)
+    ap.add_argument("--porous", type=int, default=0, metavar="SIDE",
+                    help="time a porous box of SIDE^3 cells (spheres of radius 6-10, porosity "
+                         "0.7, seed 1) instead of the duct")
     ap.add_argument("--steady", action="store_true",
                     help="also run both models from rest to steady state and report the time")
     ap.add_argument("--steady-tol", type=float, default=1e-6)
@@ -589,6 +614,9 @@ def main(argv=None):
     args = ap.parse_args(argv)
     NX, NY, NZ = args.nx, args.ny, args.nz
     LATTICE, STORAGE = args.lattice, args.storage
+    POROUS = args.porous
+    if POROUS:
+        NX = NY = NZ = POROUS
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if not set(args.serve_storage.split(",")) <= {"F32", "F64", "F16", "BF16"}:

@@ -376,20 +376,24 @@ __device__ __forceinline__ void cell_xyz(const KParams& kp, int idx, int& x, int
 #ifndef BLBM_WARP_UNIFORM_GATHER
 #define BLBM_WARP_UNIFORM_GATHER 1
 #endif
+// self = true loads the cell's own populations, plane by plane (all offsets
+// 0; lk must be 0): the copy-through of a solid cell.
 template <class L, class S, class Src>
 __device__ __forceinline__ void gather(const KParams& kp, const Src& P, uint32_t lk,
-                                       int idx, typename Store<S>::R (&v)[L::Q]) {
+                                       int idx, typename Store<S>::R (&v)[L::Q],
+                                       bool self = false) {
     const int nx = kp.nx, ny = kp.ny, nz = kp.nz;
     int x, y, z;
     cell_xyz(kp, idx, x, y, z);
     // offsets from idx to the source cell x - c for c = +1 (m) and c = -1 (p)
     const int sy = nx, sz = nx * ny;
-    const int dxm = (x == 0) ? nx - 1 : -1;
-    const int dxp = (x == nx - 1) ? -(nx - 1) : 1;
-    const int dym = (y == 0) ? (ny - 1) * sy : -sy;
-    const int dyp = (y == ny - 1) ? -(ny - 1) * sy : sy;
-    const int dzm = (z == 0) ? (nz - 1) * sz : -sz;
-    const int dzp = (z == nz - 1) ? -(nz - 1) * sz : sz;
+    int dxm = (x == 0) ? nx - 1 : -1;
+    int dxp = (x == nx - 1) ? -(nx - 1) : 1;
+    int dym = (y == 0) ? (ny - 1) * sy : -sy;
+    int dyp = (y == ny - 1) ? -(ny - 1) * sy : sy;
+    int dzm = (z == 0) ? (nz - 1) * sz : -sz;
+    int dzp = (z == nz - 1) ? -(nz - 1) * sz : sz;
+    if (self) dxm = dxp = dym = dyp = dzm = dzp = 0;
     auto offset = [&](auto I) {
         constexpr int i = decltype(I)::value;
         constexpr int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
@@ -798,12 +802,18 @@ template <int MODEL, class S, int BLOCK> constexpr int step_min_blocks() {
 // One cell of one time step: pull, collide, store; on check steps the cell's
 // contributions to the flow-rate and residual sums go to acc.  Shared by the
 // single-domain and the batched kernels so both do identical arithmetic.
+// fluid = false (plain steps only) copies a solid cell's populations through
+// unchanged, the step's definition for solid cells: a warp that holds fluid
+// cells then writes whole 32-byte sectors.  A sector the stores cover only in
+// part costs a DRAM read before its write; at the edges of a porous medium's
+// grains that doubled the reads.
 template <class L, int MODEL, class S, bool CHECK, class Src, class Dst>
 __device__ __forceinline__ void cell_step(const KParams& kp, const Coef<typename Store<S>::R>& c,
                                           const Src& src, const Dst& dst, uint32_t lk, int idx,
                                           typename Store<S>::R* __restrict__ tau,
                                           typename Store<S>::R* __restrict__ usnap, uint32_t rnd,
-                                          typename Store<S>::R (&acc)[kNumStats]) {
+                                          typename Store<S>::R (&acc)[kNumStats],
+                                          bool fluid = true) {
     using R = typename Store<S>::R;
     // check steps: the previous snapshot is read first, so its latency overlaps
     // the gather (after the population stores the compiler could not move
@@ -814,14 +824,16 @@ __device__ __forceinline__ void cell_step(const KParams& kp, const Coef<typename
         for (int d = 0; d < 3; ++d) up[d] = usnap[(int64_t)d * kp.plane + idx];
     }
     R f[L::Q];
-    gather<L, S>(kp, src, lk, idx, f);
-    R drho, ur[3];
-    if constexpr (MODEL != LBM_MODEL_IR) {
-        R t = tau[idx];
-        collide_pr<L, S, MODEL == kModelPRImplicit>(c, kp.flags, f, t, drho, ur);
-        tau[idx] = t;
-    } else {
-        collide_ir<L, S>(c, kp.flags, f, drho, ur);
+    gather<L, S>(kp, src, fluid ? lk : 0u, idx, f, !fluid);
+    R drho = R(0), ur[3] = {R(0), R(0), R(0)};
+    if (fluid) {
+        if constexpr (MODEL != LBM_MODEL_IR) {
+            R t = tau[idx];
+            collide_pr<L, S, MODEL == kModelPRImplicit>(c, kp.flags, f, t, drho, ur);
+            tau[idx] = t;
+        } else {
+            collide_ir<L, S>(c, kp.flags, f, drho, ur);
+        }
     }
     // rest population, then opposite pairs (i, i + 1), one random word each
     Store<S>::template st<L, 0>(dst.template at<0>(idx), f[0], rnd);
@@ -847,6 +859,14 @@ __device__ __forceinline__ void cell_step(const KParams& kp, const Coef<typename
     }
 }
 
+// Plain steps in which solid cells of warps holding fluid cells copy their
+// populations through (cell_step, fluid = false).  The PR step of the 16-bit
+// forms is left out: there the copy path's registers cost more spills on the
+// duct (about 6 %) than the whole sectors gain in porous media (about 6 %).
+template <int MODEL, class S> __host__ __device__ constexpr bool copy_through() {
+    return !(MODEL != LBM_MODEL_IR && sizeof(S) == 2);
+}
+
 // BLOCK: threads per block, chosen per (lattice, model, storage, size class)
 // by the tuning table; check steps always run with kBlock so their reduction
 // order does not depend on the tuning.
@@ -870,16 +890,24 @@ k_step(const KArgs a, const SrcPlanes<S> src, const DstPlanes<S> dst,
     }
     const uint32_t lk = inside ? __ldg(links + idx) : kSolidBit;
     const bool active = !(lk & kSolidBit);
-    if constexpr (!CHECK) {
-        if (!active) return;
-    }
     R acc[kNumStats];
-    if constexpr (CHECK) {
+    if constexpr (!CHECK) {
+        if constexpr (copy_through<MODEL, S>()) {
+            // a warp without fluid cells has nothing to do; in any other warp
+            // the solid cells inside the domain copy their populations through
+            if (!__any_sync(__activemask(), active) || !inside) return;
+            cell_step<L, MODEL, S, false>(kp, coef<R>(a), src, dst, lk, idx, tau, usnap, rnd, acc,
+                                          active);
+        } else {
+            if (!active) return;
+            cell_step<L, MODEL, S, false>(kp, coef<R>(a), src, dst, lk, idx, tau, usnap, rnd, acc);
+        }
+    } else {
 #pragma unroll
         for (int k = 0; k < kNumStats; ++k) acc[k] = R(0);
+        if (active) cell_step<L, MODEL, S, true>(kp, coef<R>(a), src, dst, lk, idx, tau, usnap, rnd, acc);
+        block_sum_store(acc, partials + (int64_t)blockIdx.x * kNumStats);
     }
-    if (active) cell_step<L, MODEL, S, CHECK>(kp, coef<R>(a), src, dst, lk, idx, tau, usnap, rnd, acc);
-    if constexpr (CHECK) block_sum_store(acc, partials + (int64_t)blockIdx.x * kNumStats);
 }
 
 // ---------------------------------------------------------------------------
@@ -1009,18 +1037,26 @@ __device__ __forceinline__ void batch_tile(const BatchDesc& D, int tile, int pha
     }
     const uint32_t lk = inside ? __ldg(D.links + idx) : kSolidBit;
     const bool active = !(lk & kSolidBit);
-    if constexpr (!CHECK) {
-        if (!active) return;
-    }
     R acc[kNumStats];
-    if constexpr (CHECK) {
+    if constexpr (!CHECK) {
+        // as in k_step: solid cells of a warp with fluid cells copy through
+        if constexpr (copy_through<MODEL, S>()) {
+            if (!__any_sync(__activemask(), active) || !inside) return;
+            cell_step<L, MODEL, S, false>(kp, bcoef<R>(D), src, dst, lk, idx, (R*)D.tau,
+                                          (R*)D.usnap, rnd, acc, active);
+        } else {
+            if (!active) return;
+            cell_step<L, MODEL, S, false>(kp, bcoef<R>(D), src, dst, lk, idx, (R*)D.tau,
+                                          (R*)D.usnap, rnd, acc);
+        }
+    } else {
 #pragma unroll
         for (int k = 0; k < kNumStats; ++k) acc[k] = R(0);
+        if (active)
+            cell_step<L, MODEL, S, true>(kp, bcoef<R>(D), src, dst, lk, idx, (R*)D.tau,
+                                         (R*)D.usnap, rnd, acc);
+        block_sum_store(acc, partials + (int64_t)tile * kNumStats);
     }
-    if (active)
-        cell_step<L, MODEL, S, CHECK>(kp, bcoef<R>(D), src, dst, lk, idx, (R*)D.tau, (R*)D.usnap,
-                                      rnd, acc);
-    if constexpr (CHECK) block_sum_store(acc, partials + (int64_t)tile * kNumStats);
 }
 
 // Batch step: the CTAs walk the tiles of every domain of the group (tile t,
@@ -1041,8 +1077,12 @@ __device__ __forceinline__ void batch_tile(const BatchDesc& D, int tile, int pha
 #ifndef BLBM_BATCH_PR32_MINB
 #define BLBM_BATCH_PR32_MINB 4
 #endif
+#ifndef BLBM_BATCH_IR16_MINB
+#define BLBM_BATCH_IR16_MINB 5
+#endif
 template <int MODEL, class S, bool CHECK> constexpr int batch_min_blocks() {
-    return (MODEL == LBM_MODEL_IR || CHECK) ? 0
+    return CHECK ? 0
+         : MODEL == LBM_MODEL_IR ? (sizeof(S) == 2 ? BLBM_BATCH_IR16_MINB : 0)
          : sizeof(S) == 2 ? BLBM_BATCH_PR_MINB
          : sizeof(S) == 4 ? BLBM_BATCH_PR32_MINB : 0;
 }
