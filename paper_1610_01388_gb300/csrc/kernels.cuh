@@ -1068,9 +1068,11 @@ __device__ __forceinline__ void batch_tile(const BatchDesc& D, int tile, int pha
 // take 72 registers and FP32 storage 70 (the descriptor's coefficients are
 // loaded, not kernel-parameter operands), leaving 3 blocks; on a single
 // D3Q27 duct the FP32 PR batch step measured 170 us without and 154 us with
-// the budget.  IR, check steps and FP64 are left to the allocator.
-// BLBM_BATCH_PR_MINB (16-bit) / BLBM_BATCH_PR32_MINB (FP32) override at build
-// time.
+// the budget.  Plain IR steps of the 16-bit forms keep 5 blocks (48
+// registers; their copy-through path takes 58 and 4 blocks otherwise).  FP32
+// IR, check steps and FP64 are left to the allocator.  BLBM_BATCH_PR_MINB
+// (16-bit PR), BLBM_BATCH_PR32_MINB (FP32 PR) and BLBM_BATCH_IR16_MINB
+// override at build time.
 #ifndef BLBM_BATCH_PR_MINB
 #define BLBM_BATCH_PR_MINB 4
 #endif
