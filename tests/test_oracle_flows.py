@@ -238,3 +238,22 @@ def test_startup_transient_pr_fluctuates_ir_damps(lat):
     w_ir, low_ir = _startup_profile_stats("IR", lat, 0.0)
     assert low_pr < 0.0 < low_ir
     assert w_pr > 2.0 * w_ir
+
+
+@pytest.mark.parametrize("lat", ["D3Q19", "D3Q27"])
+@pytest.mark.parametrize("model", ["PR", "IR"])
+def test_solid_cells_keep_their_populations(lat, model):
+    """A step defines nothing for solid cells: whatever they hold is carried
+    through unchanged (the GPU kernels rely on this when a warp stores a
+    solid cell's own populations back), while fluid cells next to them still
+    relax."""
+    mask, _ = W.porous_mask(16, porosity=0.7, r_min=3.0, r_max=4.0, seed=3)
+    p = oracle.params(model=model, nu_p=0.1, sigma_y=1e-5, m=1e6, g=(1e-5, 0, 0))
+    st = oracle.State(lat, p, mask)
+    st.f[:] = W.random_populations(st.w, st.N, amplitude=0.05, seed=9)
+    f0 = st.f.copy()
+    st.step(3)
+    solid = mask.reshape(-1) != 0
+    assert solid.any() and (~solid).any()
+    assert np.array_equal(st.f[:, solid], f0[:, solid])
+    assert not np.array_equal(st.f[:, ~solid], f0[:, ~solid])
