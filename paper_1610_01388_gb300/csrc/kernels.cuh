@@ -373,6 +373,8 @@ __device__ __forceinline__ void cell_xyz(const KParams& kp, int idx, int& x, int
 
 // ---------------------------------------------------------------------------
 // streaming (pull) with halfway bounce-back
+// 1: the gather path is chosen per warp (see gather); 0 restores the
+// per-thread choice, for comparison builds.
 #ifndef BLBM_WARP_UNIFORM_GATHER
 #define BLBM_WARP_UNIFORM_GATHER 1
 #endif
