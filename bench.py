@@ -4,17 +4,25 @@ Workload: 3D square duct, D3Q27, 256 (x, streamwise, periodic) x 128 x 128
 cells with solid rows y = 0 and z = 0 (127 x 127 fluid cross-section,
 4,129,024 fluid cells), body force along x, Bn = 2 (a-posteriori, mapped to
 the yield stress through the Mosolov-Miasnikov duct formula), nu_p = 0.1,
-FP32 population storage, started from rest.  One bench "step" is one lattice
-time step of BOTH Bingham models on their own copy of the duct (PR with
-m = 1e6 and IR), so both fused kernels and the check-step reductions (every
-100 steps) are exercised.  The metric is MLUPS: fluid-cell updates per second
-(all_cell_mlups counts the solid cells too).
+FP32 population storage, started from rest.  One bench "step" is one pass of
+the whole hot path for BOTH Bingham models, each on its own copy of the duct
+(PR with m = 1e6 and IR): one check interval of 100 lattice time steps, 99
+plain fused stream-and-collide steps and one check step that also computes
+the flow rate and the residual (with its FP64 finaliser).  The metric is
+MLUPS: fluid-cell updates per second (all_cell_mlups counts the solid cells
+too).
 
 Timing: W untimed warm-up steps, then K timed steps bracketed by a barrier and
 cudaDeviceSynchronize, measured with CUDA events on the solvers' stream (the
 IR phase and the PR phase each have their own events, which gives each
 kernel's average launch duration).  The populations (2 x 905 MB) are far
 larger than L2, so no flush is needed between steps.
+
+Also reported, outside the timed region: the porous box of the porous-medium
+workload (256^3, D3Q19, FP32 and FP16 storage, both models) with its own
+roofline, the same metric end to end through the C ABI with host buffers,
+and the continuous-batching server on a Poisson stream of independent solves
+run to steady state.
 
 --impl reference times the FP64 CPU oracle (the correctness reference) on
 the host cores, on a bounded sample of the same duct, one sample per step.
@@ -46,7 +54,7 @@ STORAGE_DTYPE = {"F32": "f32", "F64": "f64", "F16": "f16 storage / f32 arithmeti
 NU_P = 0.1
 BN = 2.0
 M_PR = 1e6
-CHECK_EVERY = 100
+CHECK_EVERY = 100     # lattice steps per check step; one bench step = one check interval
 SAMPLE_NX = 4          # x-extent of the oracle's sample of the duct (periodic along x)
 POROUS = 0             # > 0: a porous box of this side replaces the duct
 
@@ -67,6 +75,8 @@ def workload_config(extra=None):
                        "cross-section), "
                        f"PR (m={M_PR:g}) + IR per step, Bn={BN:g}, nu_p={NU_P}, {STORAGE} populations, "
                        f"check step every {CHECK_EVERY}",
+           "bench_step": f"{CHECK_EVERY} lattice time steps of each model: {CHECK_EVERY - 1} plain "
+                         "fused steps + 1 check step (flow rate, residual, FP64 finaliser)",
            "lattice": LATTICE, "nx": NX, "ny": NY, "nz": NZ, "models": ["PR", "IR"],
            "storage": STORAGE,
            "l2": f"inputs {'larger' if pop_mb > 129 else 'smaller'} than L2 (populations per model: "
@@ -93,10 +103,15 @@ def workload_mask(nx=None):
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
-# step kernels on this workload (256x128x128 duct), from one one-pass ncu
-# capture of this script.  Keyed by storage, model, block size and cells per
-# thread; valid only for the device-code sources they were captured with
-# (KERNEL_FINGERPRINT), reported as null once any of them changes.
+# step kernels, from ncu captures of this script (the commands are in the
+# profiles/ summaries).  NCU_TRAFFIC: the 256x128x128 D3Q27 duct, keyed by
+# storage, model, block size and cells per thread.  NCU_TRAFFIC_POROUS: the
+# porous box of the porous record, captured on a 160^3 box of the same
+# generator (radius 6-10, porosity 0.7, seed 1) and scaled to the 256^3 box
+# by its fluid-cell count, keyed by storage and model.  Both are valid only
+# for the device-code sources they were captured with (KERNEL_FINGERPRINT)
+# and are reported as null once any of those sources changes.
+NCU_TRAFFIC_POROUS = {}
 NCU_TRAFFIC = {
     ("F32", "IR", 128, 1): 855728463, ("F32", "IR", 256, 1): 855565948, ("F32", "IR", 512, 1): 857448187,
     ("F32", "IR", 128, 2): 855414940, ("F32", "IR", 256, 2): 857265614,
@@ -126,11 +141,13 @@ def kernel_fingerprint():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(storage, model, block, cpt, override=None):
+def ncu_traffic(storage, model, block, cpt, override=None, workload="duct"):
     if override is not None:
         return override
     if KERNEL_FINGERPRINT is None or kernel_fingerprint() != KERNEL_FINGERPRINT:
         return None
+    if workload == "porous":
+        return NCU_TRAFFIC_POROUS.get((storage, model))
     if POROUS or (LATTICE, NX, NY, NZ) != ("D3Q27", 256, 128, 128):
         return None
     return NCU_TRAFFIC.get((storage, model, block, cpt))
@@ -280,30 +297,35 @@ def run_ours(args):
 
     # warm-up (also captures the CUDA graphs)
     for model in ("IR", "PR"):
-        solvers[model].step(args.warmup)
+        solvers[model].step(args.warmup * CHECK_EVERY)
     torch.cuda.synchronize(dev)
 
-    K = args.steps
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    K = args.steps                 # bench steps
+    NL = K * CHECK_EVERY           # lattice time steps per model
+    # events between bench steps: IR's K bench steps, then PR's
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * K + 1)]
     clocks = ClockSampler(local)
     clocks.start()
     barrier()
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     ev[0].record(stream)
-    solvers["IR"].step(K)
-    ev[1].record(stream)
-    solvers["PR"].step(K)
-    ev[2].record(stream)
+    for m, model in enumerate(("IR", "PR")):
+        for k in range(K):
+            solvers[model].step(CHECK_EVERY)
+            ev[m * K + k + 1].record(stream)
     torch.cuda.synchronize(dev)
     t1 = time.perf_counter()
     barrier()
     clk = clocks.stop()
-    ms_ir = ev[0].elapsed_time(ev[1])
-    ms_pr = ev[1].elapsed_time(ev[2])
+    ms_ir = ev[0].elapsed_time(ev[K])
+    ms_pr = ev[K].elapsed_time(ev[2 * K])
+    # per bench step (both models): the IR and the PR part of step k
+    step_ms = [ev[k].elapsed_time(ev[k + 1]) + ev[K + k].elapsed_time(ev[K + k + 1])
+               for k in range(K)]
     ms_total = ms_ir + ms_pr
     max_s = reduce_max(ms_total / 1e3, dev if ws > 1 else None)
-    value = aggregate(2.0 * nfluid * K, max_s, ws)
+    value = aggregate(2.0 * nfluid * NL, max_s, ws)
 
     # residual sanity (the run must stay finite)
     for model in ("IR", "PR"):
@@ -312,10 +334,10 @@ def run_ours(args):
     info_ir = solvers["IR"].info
     info_pr = solvers["PR"].info
     peak, peak_kind = measured_hbm_peak()
-    launches_per_model = K + K // CHECK_EVERY   # step kernels + check-step finalisers
+    launches_per_model = NL + NL // CHECK_EVERY   # step kernels + check-step finalisers
     per = {}
     for model, ms, inf in (("IR", ms_ir, info_ir), ("PR", ms_pr, info_pr)):
-        t_launch = ms / 1e3 / K
+        t_launch = ms / 1e3 / NL
         gbs = inf.bytes_per_fluid_update * nfluid / t_launch / 1e9
         per[model] = {"bytes_per_update": inf.bytes_per_fluid_update, "launch_us": t_launch * 1e6,
                       "achieved_gbs": gbs, "frac": gbs / peak,
@@ -340,12 +362,19 @@ def run_ours(args):
 
     e2e = run_e2e(args, mask, nfluid, g, sy, dev)
     steady = run_steady(args, mask, nfluid, g, sy) if args.steady else None
+    porous = run_porous_record(args) if (args.porous_record > 0 and not POROUS) else None
     serving = None
     if args.serve_requests > 0:
         serving = {"form": "served FP16-offset storage (stochastic rounding) vs FP32, batched",
                    "budget_gb": 120, "rate_per_s": args.serve_rate,
-                   "tolerance": args.serve_tolerance, "step_cap": args.serve_max_steps,
+                   "steady_state": (f"{args.serve_criterion} criterion: "
+                                    + ("relative change of the mean velocity vector"
+                                       if args.serve_criterion == "flow" else "field residual")
+                                    + f" between check steps {args.serve_check_every} steps "
+                                      f"apart < {args.serve_tolerance:g}"),
+                   "step_cap": args.serve_max_steps,
                    "mix": SERVE_MIX_FULL if args.serve_full else SERVE_MIX,
+                   "plain_fp32_single_domain_mlups": round(value, 1),
                    "runs": [run_serving(args, st) for st in args.serve_storage.split(",")]}
     cpu = run_cpu_baseline(args) if (rank == 0 and ws == 1 and not args.no_cpu) else None
     if rank == 0:
@@ -355,8 +384,10 @@ def run_ours(args):
                 "dtype": STORAGE_DTYPE[STORAGE], "data": "synthetic",
                 "config": workload_config({"per_rank": "independent duct pair per GPU",
                                            "fluid_cells": nfluid, "autotuned": tuned}),
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "serving": serving,
-                "time_to_steady": steady,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "porous": porous,
+                "serving": serving, "time_to_steady": steady,
+                "ms_per_step_median": round(statistics.median(step_ms), 5),
+                "ms_per_step_spread": [round(min(step_ms), 5), round(max(step_ms), 5)],
                 "gpu_launches": 2 * launches_per_model, "clocks": clk,
                 "all_cell_mlups": round(value * mask.size / nfluid, 1),
                 "wall_s_timed_region": round(t1 - t0, 4)}
@@ -398,7 +429,7 @@ def run_e2e(args, mask, nfluid, g, sy, dev):
     host (D2H of rho and u), lbm_destroy; all inside the timed region."""
     import torch
     from paper_1610_01388_gb300 import lbm
-    K = args.e2e_steps if args.e2e_steps > 0 else args.steps
+    K = (args.e2e_steps if args.e2e_steps > 0 else args.steps) * CHECK_EVERY   # lattice steps
     rho = np.empty(mask.size)
     u = np.empty((3, mask.size))
     torch.cuda.synchronize(dev)
@@ -418,17 +449,85 @@ def run_e2e(args, mask, nfluid, g, sy, dev):
     t1 = time.perf_counter()
     ws, _, _ = dist_env()
     max_s = reduce_max(t1 - t0, dev if ws > 1 else None)
+    nb = K // CHECK_EVERY                                      # bench steps
     return {"value": round(aggregate(2.0 * nfluid * K, max_s, ws), 1), "unit": "MLUPS",
-            "h2d_bytes_per_step": round(2 * mask.size / K, 3),
-            "d2h_bytes_per_step": round(2 * 4 * 8 * mask.size / K, 3),
-            "steps": K, "what": "per model: lbm_create (host mask H2D) + lbm_step(K) + "
-                                "lbm_fields (rho,u D2H) + lbm_destroy, inside the timed region"}
+            "h2d_bytes_per_step": round(2 * mask.size / nb, 3),
+            "d2h_bytes_per_step": round(2 * 4 * 8 * mask.size / nb, 3),
+            "steps": nb, "lattice_steps": K,
+            "what": "per model: lbm_create (host mask H2D) + lbm_step(lattice steps) + "
+                    "lbm_fields (rho,u D2H) + lbm_destroy, inside the timed region"}
+
+
+def run_porous_record(args):
+    """The porous-medium workload outside the timed region: a 256^3 periodic
+    box of random non-overlapping spheres (radius 6-10, porosity 0.7, seed 1),
+    D3Q19, both models, FP32 and FP16 storage, each timed with CUDA events
+    over args.porous_steps lattice steps after one check interval of warm-up.
+    The dense layout keeps every cell, so a warp with any fluid cell moves
+    all 32 cells' populations: touched_over_fluid is that floor of the
+    traffic relative to the algorithmic (fluid-cell) bytes."""
+    import torch
+    from paper_1610_01388_gb300 import lbm
+    from paper_1610_01388_gb300 import workloads as W
+    side = args.porous_record
+    mask, info = W.porous_mask(side, porosity=0.7, r_min=6.0, r_max=10.0, seed=1)
+    flat = (mask.reshape(-1) == 0).astype(np.int64)
+    nfluid = int(flat.sum())
+    warp = np.arange(flat.size) // 32
+    fluid_per_warp = np.bincount(warp, weights=flat)
+    cells_per_warp = np.bincount(warp)
+    touched = int(cells_per_warp[fluid_per_warp > 0].sum())
+    prm = W.porous_params(nu_p=NU_P, d_mean=16.0, g=2e-5, bn=BN)
+    peak, kind = measured_hbm_peak()
+    st = torch.cuda.current_stream()
+    kernels = {}
+    for storage in ("F32", "F16"):
+        for model in ("IR", "PR"):
+            s = lbm.Solver("D3Q19", mask, model=model, storage=storage, mu_p=NU_P,
+                           sigma_y=prm["sigma_y"], m=M_PR, g=(prm["g"], 0.0, 0.0),
+                           check_every=CHECK_EVERY, use_torch=True)
+            s.step(CHECK_EVERY)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(st)
+            s.step(args.porous_steps)
+            e1.record(st)
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1) / 1e3 / args.porous_steps
+            b = s.info.bytes_per_fluid_update
+            s.residual()
+            s.close()
+            gbs = b * nfluid / t / 1e9
+            kernels[f"{model}/{storage}"] = {
+                "kernel": f"k_step<D3Q19,{model},{STORAGE_CTYPE[storage]}>",
+                "launch_us": round(t * 1e6, 2), "mlups": round(nfluid / t / 1e6, 1),
+                "bytes_per_fluid_update": b, "achieved_gbs": round(gbs, 1),
+                "frac": round(gbs / peak, 4),
+                "frac_of_touched": round(gbs * touched / nfluid / peak, 4),
+                "traffic": ncu_traffic(storage, model, 256, 1, None, workload="porous")}
+    roof = {}
+    for storage in ("F32", "F16"):
+        dom = max(("IR", "PR"), key=lambda m: kernels[f"{m}/{storage}"]["launch_us"])
+        k = kernels[f"{dom}/{storage}"]
+        roof[storage] = {"bound": "hbm", "kernel": k["kernel"] + " (dominant by time)",
+                         "achieved": k["achieved_gbs"], "peak": peak,
+                         "peak_kind": f"{kind} (copy bandwidth)", "unit": "GB/s",
+                         "frac": k["frac"], "traffic": k["traffic"],
+                         "bytes_per_fluid_update": k["bytes_per_fluid_update"],
+                         "fluid_cells_per_launch": nfluid}
+    return {"workload": f"porous box D3Q19 {side}^3 (random non-overlapping spheres, radius "
+                        f"6-10, porosity {info['porosity']:.3f}, seed 1), Bn={BN:g} a priori, "
+                        f"nu_p={NU_P}, PR m={M_PR:g}; 256 threads per block, check step every "
+                        f"{CHECK_EVERY}",
+            "fluid_cells": nfluid, "cells": int(flat.size),
+            "touched_over_fluid": round(touched / nfluid, 4),
+            "lattice_steps_timed": args.porous_steps, "roofline": roof, "kernels": kernels}
 
 
 # --- serving ----------------------------------------------------------------------
 
-SERVE_MIX = ("D2Q9 channels 4 x (17..257), D3Q19/D3Q27 ducts 64 x (33..97)^2, "
-             "D3Q19/D3Q27 porous boxes (32..64)^3 porosity 0.7 radius 4-6; Bn U[0.1,10]; PR/IR")
+SERVE_MIX = ("D2Q9 channels 32 x (17..65), D3Q19/D3Q27 ducts 32 x (17..49)^2, "
+             "D3Q19/D3Q27 porous boxes (24..48)^3 porosity 0.7 radius 3-5; Bn U[0.1,10]; PR/IR")
 SERVE_MIX_FULL = ("D2Q9 channels 4 x (17..257), D3Q19/D3Q27 ducts 64 x (33..193)^2, "
                   "D3Q19/D3Q27 porous boxes (64..256)^3 (sides in steps of 16, 2 seeded "
                   "geometries per side) porosity 0.7 radius 6-10; Bn U[0.1,10]; PR/IR")
@@ -438,38 +537,51 @@ def _serve_sizes(args):
     if args.serve_full:
         return dict(duct_sides=(32, 192), porous_sides=(64, 256), porous_radius=(6.0, 10.0),
                     porous_pool=2)
-    return {}
+    # a mix whose solves reach steady state within the bench's minutes: the
+    # slowest mode of a channel or duct of width H decays over ~H^2 / nu steps
+    return dict(channel_widths=(16, 64), channel_length=32, duct_sides=(16, 48),
+                duct_length=32, porous_sides=(24, 48), porous_radius=(3.0, 5.0))
 
 
 def run_serving(args, storage):
     """A Poisson stream of independent solves (channels, ducts, porous boxes;
     Bn uniform in [0.1, 10]; PR or IR) through the continuous-batching server
     under a 120 GB budget: requests are submitted at their arrival times while
-    the server steps everything admitted in 200-step chunks (check every 100).
-    Latency = completion - arrival; time to steady state is that latency for
-    the requests whose residual fell below the tolerance."""
+    the server steps everything admitted in chunks of args.serve_chunk steps
+    (check every 100) and retires each solve at steady state (the criterion
+    of --serve-criterion between consecutive check steps below the
+    tolerance) or at the step cap.  Latency = completion - arrival; time to
+    steady state is that latency for the converged requests.  Accuracy: a
+    sample of the served requests (the first two of each kind) is solved
+    again on the plain FP32 single-domain path (lbm_step) for the same number
+    of steps, and the relative L2 difference of the velocity fields is
+    reported."""
     from paper_1610_01388_gb300 import lbm
     from paper_1610_01388_gb300 import workloads as W
     reqs = W.serving_requests(n=args.serve_requests, rate=args.serve_rate, seed=7,
                               storage=storage, max_steps=args.serve_max_steps,
-                              tolerance=args.serve_tolerance, **_serve_sizes(args))
+                              tolerance=args.serve_tolerance, criterion=args.serve_criterion,
+                              **_serve_sizes(args))
+    sample = []
+    for kind in ("channel", "duct", "porous"):
+        sample += [i for i, r in enumerate(reqs) if r["kind"] == kind][:2]
     schedule = None
     if not args.no_tune:
         # the batch schedule, tuned on a mix drawn from the same generator
         # (another seed), outside the timed region
         from paper_1610_01388_gb300 import autotune
-        sample = W.serving_requests(n=48, rate=args.serve_rate, seed=8, storage=storage,
-                                    max_steps=args.serve_max_steps,
-                                    tolerance=args.serve_tolerance, **_serve_sizes(args))
+        tune_mix = W.serving_requests(n=48, rate=args.serve_rate, seed=8, storage=storage,
+                                      max_steps=args.serve_max_steps,
+                                      tolerance=args.serve_tolerance, **_serve_sizes(args))
         mix = [(r["lattice"], r["mask"], dict(model=r["model"], storage=r["storage"],
                                               mu_p=r["mu_p"], sigma_y=r["sigma_y"], m=r["m"],
-                                              g=r["g"])) for r in sample]
+                                              g=r["g"])) for r in tune_mix]
         tuned = autotune.tune_batch(mix)
         schedule = {k: v for k, v in tuned.items() if k != "tried"}
         schedule["us_per_step_untuned"] = round(tuned["tried"]["base"] * 1e6, 1)
         schedule["seconds_per_step"] = round(schedule["seconds_per_step"] * 1e6, 1)
         schedule["us_per_step"] = schedule.pop("seconds_per_step")
-    srv = lbm.Server(120 * (1 << 30), check_every=100)
+    srv = lbm.Server(120 * (1 << 30), check_every=args.serve_check_every)
     t0 = srv.now()
     ids = []
     k = 0
@@ -478,7 +590,8 @@ def run_serving(args, storage):
         while k < len(reqs) and reqs[k]["arrival"] <= now:
             r = reqs[k]
             ids.append(srv.submit(r["lattice"], r["mask"], tolerance=r["tolerance"],
-                                  max_steps=r["max_steps"], model=r["model"],
+                                  max_steps=r["max_steps"], criterion=r["criterion"],
+                                  keep_fields=k in sample, model=r["model"],
                                   storage=r["storage"], mu_p=r["mu_p"], sigma_y=r["sigma_y"],
                                   m=r["m"], g=r["g"]))
             k += 1
@@ -488,15 +601,38 @@ def run_serving(args, storage):
                 break
             time.sleep(max(0.0, reqs[k]["arrival"] - (srv.now() - t0)))
             continue
-        srv.advance(200)
+        srv.advance(args.serve_chunk)
     res = [srv.result(i) for i in ids]
+    served_u = {i: srv.fields(ids[i], reqs[i]["mask"].shape if reqs[i]["mask"].ndim == 3
+                              else (1,) + reqs[i]["mask"].shape)[1] for i in sample}
     srv.close()
+    acc = []
+    for i in sample:
+        r = reqs[i]
+        ref = lbm.Solver(r["lattice"], r["mask"], model=r["model"], storage="F32", mu_p=r["mu_p"],
+                         sigma_y=r["sigma_y"], m=r["m"], g=r["g"],
+                         check_every=args.serve_check_every)
+        ref.step(res[i].steps)
+        _, uref = ref.fields()
+        ref.close()
+        fl = (r["mask"] if r["mask"].ndim == 3 else r["mask"][None]) == 0
+        a, b = served_u[i][:, fl], uref.reshape(served_u[i].shape)[:, fl]
+        acc.append({"kind": r["kind"], "lattice": r["lattice"], "model": r["model"],
+                    "steps": int(res[i].steps),
+                    "rel_l2_u_vs_fp32_single_domain": float(np.linalg.norm(a - b) / np.linalg.norm(b))})
     lat = np.array([r.t_done - r.t_submit for r in res])
     conv = np.array([r.state == lbm.LBM_REQ_CONVERGED for r in res])
     upd = sum(r.fluid_cells * r.steps for r in res)
     span = max(r.t_done for r in res) - min(r.t_submit for r in res)
     tts = lat[conv]
+    errs = [a["rel_l2_u_vs_fp32_single_domain"] for a in acc]
     return {"storage": storage, "requests": len(res), "served_solves_per_s": round(len(res) / span, 3),
+            "converged_fraction": round(float(conv.mean()), 4),
+            "steps_to_steady_p50": int(np.percentile([r.steps for r, c in zip(res, conv) if c], 50))
+            if conv.any() else None,
+            "accuracy": {"max_rel_l2_u_vs_fp32_single_domain": max(errs) if errs else None,
+                         "bar": 1e-3 if storage in ("F16", "BF16") else 1e-5,
+                         "requests": acc},
             "latency_p50_s": round(float(np.percentile(lat, 50)), 4),
             "latency_p99_s": round(float(np.percentile(lat, 99)), 4),
             "time_to_steady_p50_s": round(float(np.percentile(tts, 50)), 4) if tts.size else None,
@@ -580,8 +716,9 @@ def main(argv=None):
     global NX, NY, NZ, LATTICE, STORAGE, POROUS
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
-    ap.add_argument("--warmup", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=20,
+                    help=f"timed bench steps ({CHECK_EVERY} lattice steps of each model each)")
+    ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--e2e-steps", type=int, default=0)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
@@ -590,8 +727,16 @@ def main(argv=None):
     ap.add_argument("--serve-requests", type=int, default=300,
                     help="requests in the serving leg (0 skips it)")
     ap.add_argument("--serve-rate", type=float, default=150.0, help="Poisson arrival rate, 1/s")
-    ap.add_argument("--serve-max-steps", type=int, default=3000)
-    ap.add_argument("--serve-tolerance", type=float, default=1e-3)
+    ap.add_argument("--serve-max-steps", type=int, default=200_000)
+    ap.add_argument("--serve-tolerance", type=float, default=1e-5)
+    ap.add_argument("--serve-criterion", choices=["flow", "residual"], default="flow")
+    ap.add_argument("--serve-check-every", type=int, default=1000,
+                    help="steps between the check steps the steady-state test compares")
+    ap.add_argument("--serve-chunk", type=int, default=1000,
+                    help="steps per server advance (a multiple of the check interval)")
+    ap.add_argument("--porous-record", type=int, default=256, metavar="SIDE",
+                    help="side of the porous box timed beside the duct (0 skips it)")
+    ap.add_argument("--porous-steps", type=int, default=500)
     ap.add_argument("--serve-storage", default="F16,F32",
                     help="storage forms served, comma-separated, in order")
     ap.add_argument("--serve-full", action="store_true",
@@ -619,6 +764,22 @@ def main(argv=None):
         NX = NY = NZ = POROUS
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.serve_chunk < args.serve_check_every or args.serve_chunk % args.serve_check_every:
+        ap.error("--serve-chunk must be a positive multiple of --serve-check-every")
+    world = os.environ.get("WORLD_SIZE")
+    if world is not None and int(world) != args.gpus:
+        print(f"bench.py: --gpus {args.gpus} but WORLD_SIZE={world}", file=sys.stderr)
+        sys.exit(2)
+    if world is None and args.gpus > 1:
+        # one process per GPU: relaunch under torch.distributed.run
+        import socket
+        with socket.socket() as sk:
+            sk.bind(("127.0.0.1", 0))
+            port = sk.getsockname()[1]
+        argv_full = sys.argv[1:] if argv is None else list(argv)
+        os.execvp(sys.executable, [sys.executable, "-m", "torch.distributed.run", "--nnodes=1",
+                                   f"--nproc-per-node={args.gpus}", "--master-addr=127.0.0.1",
+                                   f"--master-port={port}", os.path.abspath(__file__), *argv_full])
     if not set(args.serve_storage.split(",")) <= {"F32", "F64", "F16", "BF16"}:
         ap.error("--serve-storage takes F32, F64, F16, BF16, comma-separated")
     if args.impl == "reference":

@@ -68,12 +68,16 @@ typedef enum { LBM_MODEL_PR = 0, LBM_MODEL_IR = 1 } lbm_model;
 
 /* Population storage in device memory.  Every form stores the offset
  * f_i - w_i from the rest state; the collision arithmetic is FP64 for
- * LBM_F64 and FP32 for the others. */
+ * LBM_F64 and FP32 for the others.  The 16-bit forms round stochastically on
+ * every store.  LBM_F16_OFS is the reduced-precision form: its velocity
+ * error against FP64 at equal step count measured 1.7-2.2e-4 relative L2
+ * (within 1e-3).  LBM_BF16_OFS keeps 8 significant bits and measured
+ * 1.4-1.7e-3: it does NOT meet that 1e-3 tolerance and is an option only. */
 typedef enum {
     LBM_F64 = 0,      /* double offsets */
     LBM_F32 = 1,      /* float offsets */
-    LBM_F16_OFS = 2,  /* half offsets, scaled */
-    LBM_BF16_OFS = 3  /* bfloat16 offsets, scaled */
+    LBM_F16_OFS = 2,  /* half offsets, scaled by 2^14 / w_i */
+    LBM_BF16_OFS = 3  /* bfloat16 offsets, scaled by 1 / w_i (fails the 1e-3 tolerance) */
 } lbm_storage;
 
 typedef enum {
@@ -91,6 +95,13 @@ typedef enum {
 #define LBM_FLAG_BURNETT_X 0x1u /* zero the xx components of D (PR) and of T (IR),
                                    the Burnett-suppressed variant of Secs. 4.2.1-4.2.2
                                    for flow along x */
+#define LBM_FLAG_Z_GHOSTS 0x2u  /* the solver is one z-slab of a larger domain: its
+                                   first and last z-planes are ghost planes that hold
+                                   the neighbouring slabs' boundary populations (see
+                                   lbm_halo_pack); they are never stepped and never
+                                   counted, and their mask rows are the neighbours'
+                                   own rows, so bounce-back across the slab faces is
+                                   that of the whole domain.  3D lattices, nz >= 3 */
 
 /* Rheology, forcing and run-control parameters (lattice units, rho_0 = 1). */
 typedef struct {
@@ -124,7 +135,8 @@ lbm_status lbm_params_default(lbm_params *p);
 lbm_status lbm_lattice_info(lbm_lattice lat, int *Q, int *D, int *c, double *w);
 
 /* Device bytes lbm_create_with_workspace needs for this problem (populations
- * A/B, link masks, PR tau A/B, residual snapshot, reduction partials). */
+ * A/B, link masks, the PR relaxation-time field (one, updated in place),
+ * residual snapshot, reduction partials). */
 lbm_status lbm_workspace_bytes(lbm_lattice lat, int nx, int ny, int nz,
                                const lbm_params *p, size_t *bytes);
 
@@ -181,18 +193,22 @@ lbm_status lbm_flowrate(lbm_solver *s, int axis, double *q);
 lbm_status lbm_totals(lbm_solver *s, double *mass, double momentum[3]);
 
 /* Result of the last check step (check_every > 0): residual
- * sqrt(sum |u - u_prev|^2 / sum |u|^2) against the previous check step
- * (-1 before two check steps), its step index, and the flow rate along x at
- * that step.  Returns LBM_ENONFINITE if that check step saw a non-finite
+ * sqrt(sum |u - u_prev|^2 / sum |u|^2) over fluid cells against the previous
+ * check step (-1 before two check steps), its step index, and the flow rate
+ * along x at that step.  The paper judges convergence by the relative change
+ * of U_max between steps (Sec. 4.4) and of the velocity field (Sec. 4.5.2);
+ * this residual is the L2 form of the latter.  Returns LBM_ENONFINITE if that check step saw a non-finite
  * density.  Synchronises. */
 lbm_status lbm_residual(lbm_solver *s, double *residual, int64_t *at_step, double *flow_x);
 
 /* Replace / read the population state (host, FP64 full f, Q*N, library
- * order).  Synchronises. */
+ * order).  lbm_set_populations writes both A/B buffers, so a solid cell
+ * keeps the uploaded populations through every later step (a step defines
+ * nothing for solid cells) and lbm_get_populations returns them.
+ * Synchronises. */
 lbm_status lbm_set_populations(lbm_solver *s, const double *f);
 lbm_status lbm_get_populations(lbm_solver *s, double *f);
 
-/* PR relaxation-time field (host, N doubles).  LBM_EINVAL for IR. */
 /* Full FP64 populations of n listed cells (host array of cell indices
  * x + nx (y + ny z), each in 0..cells-1; n <= 2^24), in the library's velocity
  * order: f[i * n + k] = f_i(cells[k]), a host array of Q n doubles.  A probe of
@@ -201,8 +217,52 @@ lbm_status lbm_get_populations(lbm_solver *s, double *f);
  * for the call; synchronises. */
 lbm_status lbm_get_populations_cells(lbm_solver *s, const int64_t *cells, int64_t n, double *f);
 
+/* PR relaxation-time field tau = 1/2 + 3 nu_app (eq. tau_visc), one value per
+ * cell (host, N doubles), the value the next step's strain rate uses
+ * (eq. LBM_strain_rate).  LBM_EINVAL for IR.  Synchronises. */
 lbm_status lbm_set_tau(lbm_solver *s, const double *tau);
 lbm_status lbm_get_tau(lbm_solver *s, double *tau);
+
+/* ------------------------------------------------------------------------
+ * One domain split into z-slabs (no counterpart in the paper: the method is
+ * local per cell plus streaming to the nearest neighbours, eq. (8), so a
+ * domain decomposes into slabs that exchange one plane of populations per
+ * face and step).  Each slab is a solver created with LBM_FLAG_Z_GHOSTS over
+ * its own planes plus one ghost plane on each side, whose mask rows are the
+ * neighbouring slabs' boundary rows (periodic domain: slab 0's lower
+ * neighbour is the last slab).  Before every step, for each face:
+ *   lbm_halo_pack(lower slab, 1, buf)   -- its last interior plane's c_z = +1
+ *                                          populations
+ *   lbm_halo_unpack(upper slab, 0, buf) -- into the upper slab's lower ghost
+ *   lbm_halo_pack(upper slab, 0, buf2)  -- its first interior plane's c_z = -1
+ *                                          populations
+ *   lbm_halo_unpack(lower slab, 1, buf2)-- into the lower slab's upper ghost
+ * then every slab takes one step (lbm_step(s, 1)).  The slabs then hold
+ * exactly the populations of the undivided domain (same per-cell
+ * arithmetic).  buf: a device buffer of lbm_halo_bytes() bytes, stored values
+ * in the solver's storage form (no conversion), aligned to the storage
+ * element; between processes it can travel by any transport (NCCL
+ * send/recv, peer copy), since both slabs use the same lattice and storage.
+ * Pack and unpack are asynchronous on the solver's stream and act on its
+ * current population buffer; order them against the other slab's stream.
+ * LBM_EINVAL if the solver has no ghost planes or side is not 0 or 1.
+ * ------------------------------------------------------------------------ */
+lbm_status lbm_halo_bytes(const lbm_solver *s, size_t *bytes);
+lbm_status lbm_halo_pack(lbm_solver *s, int side, void *buf_device);
+lbm_status lbm_halo_unpack(lbm_solver *s, int side, const void *buf_device);
+
+/* Offset added (modulo 2^32) to the cell index in the stochastic-rounding
+ * hash of the 16-bit storage forms, so a slab whose local cell n is cell
+ * n + offset of the whole domain draws the same random bits as the
+ * undivided domain (offset = (z0 - 1) nx ny for a slab whose first interior
+ * plane is global plane z0).  Default 0; no effect on FP32 / FP64. */
+lbm_status lbm_set_hash_offset(lbm_solver *s, int64_t offset);
+
+/* Raw sums of the last check step over the solver's fluid cells, for
+ * combining slabs: usum[a] = sum of u_real,a; du2 = sum |u - u_prev|^2;
+ * u2 = sum |u|^2 (the residual of lbm_residual is sqrt(du2 / u2), the flow
+ * rate usum[a] / L_a).  Zeros before the first check step.  Synchronises. */
+lbm_status lbm_check_sums(lbm_solver *s, double usum[3], double *du2, double *u2);
 
 /* Problem description of a live solver. */
 typedef struct {
@@ -277,8 +337,8 @@ lbm_status lbm_tuning_clear(void);   /* also resets the batch schedule below */
 /* Batch schedule (no counterpart in the paper), read by every batch (and so
  * every server) at its next lbm_batch_step:
  *   ctas_per_sm -- per (lattice, model, storage) group: 0 (default) launches
- *     one 256-thread CTA per 256-cell tile; n > 0 launches a persistent grid
- *     of min(tiles, n x SMs) CTAs that walk the tiles.  0..32.
+ *     one CTA per tile; n > 0 launches a persistent grid of min(tiles,
+ *     n x SMs) CTAs that walk the tiles.  0..32.
  *   concurrency -- 1: the captured 16-step graphs run the groups as parallel
  *     branches (they touch disjoint memory); 0 (default): one after another.
  * Results do not depend on either: the per-cell arithmetic and the order of
@@ -291,6 +351,22 @@ lbm_status lbm_tuning_get_batch(lbm_lattice lat, int32_t model, int32_t storage,
                                 int32_t *ctas_per_sm);
 lbm_status lbm_tuning_set_batch_concurrency(int32_t concurrent);
 lbm_status lbm_tuning_get_batch_concurrency(int32_t *concurrent);
+/* Plain-step tile shape of the batch kernel for a (lattice, model, storage,
+ * size class) group, size class = floor(log2(mean cells of the group's
+ * domains)): threads per CTA (128, 256, 512) x cells each thread steps one
+ * after the other (1, or 2 with 128 or 256 threads); a tile is that many
+ * consecutive cells of one domain.  A group with no entry for its class
+ * takes the entry of the nearest class set for its (lattice, model,
+ * storage), else 256 x 1.  FP64 storage and the Newton-implicit PR step
+ * always run 256 x 1 (FP64 entries other than 256 x 1 are LBM_EINVAL).
+ * Check steps always run 256-cell tiles, so results do not depend on it.
+ * lbm_tuning_get_batch_tile reports the shape a group of mean_cells cells
+ * would run and its size class. */
+lbm_status lbm_tuning_set_batch_tile(lbm_lattice lat, int32_t model, int32_t storage,
+                                     int32_t size_class, int32_t threads, int32_t cells_per_thread);
+lbm_status lbm_tuning_get_batch_tile(lbm_lattice lat, int32_t model, int32_t storage,
+                                     int64_t mean_cells, int32_t *threads,
+                                     int32_t *cells_per_thread, int32_t *size_class);
 
 /* ------------------------------------------------------------------------
  * Batched stepping of many resident domains (no counterpart in the paper: a
@@ -318,6 +394,10 @@ typedef struct {
     double flow[3];     /* flow rate along x, y, z at the last check step */
     int32_t nonfinite;  /* 1 if the last check step saw a non-finite density */
     int32_t pad;
+    double flow_change; /* |S - S_prev| / |S|, S the sums of u_real over fluid
+                           cells at the last check step and S_prev at the one
+                           before (the relative change of the mean velocity
+                           vector over check_every steps); -1 before two */
 } lbm_domain_status;
 
 lbm_status lbm_batch_create(lbm_batch **out, size_t device_budget_bytes, int32_t check_every,
@@ -347,23 +427,30 @@ void lbm_batch_destroy(lbm_batch *b);
  * request in when an earlier one does not fit), advances every running
  * solve together by nsteps (a multiple of check_every) through one batch,
  * and retires the solves that reached steady state or their step cap,
- * freeing their memory for the next admissions.  Steady state: the flow
- * rate along the body force changed by less than tolerance (relative)
- * between the last check steps of two consecutive advance calls -- the
- * integral counterpart of the paper's U_max change criterion (Sec. 4.4),
- * insensitive to per-cell rounding noise of the 16-bit storage forms.
+ * freeing their memory for the next admissions.  Steady state is judged at
+ * the last check step of each advance, between it and the check step
+ * check_every steps before (the paper judges convergence by the change of
+ * U_max between steps, Sec. 4.4, and of the velocity field, Sec. 4.5.2):
+ *   LBM_STEADY_FLOW      the mean velocity vector changed by less than
+ *                        tolerance (relative; lbm_domain_status.flow_change),
+ *                        insensitive to per-cell rounding noise of the
+ *                        16-bit storage forms;
+ *   LBM_STEADY_RESIDUAL  the field residual sqrt(sum |u - u_prev|^2 /
+ *                        sum |u|^2) is below tolerance.
  * Times are seconds on the server's monotonic clock (lbm_server_now).
  * ------------------------------------------------------------------------ */
 typedef struct lbm_server lbm_server;
+
+enum { LBM_STEADY_FLOW = 0, LBM_STEADY_RESIDUAL = 1 };
 
 typedef struct {
     int32_t lattice, nx, ny, nz;
     const uint8_t *solid_mask;  /* host, nx*ny*nz, copied at submit */
     lbm_params params;
-    double tolerance;           /* steady state: relative flow-rate change < tolerance */
+    double tolerance;           /* steady state: change per check interval < tolerance */
     int64_t max_steps;          /* step cap (> 0) */
     int32_t keep_fields;        /* keep rho and u_real of the final state on the host */
-    int32_t pad;
+    int32_t criterion;          /* LBM_STEADY_FLOW (0) or LBM_STEADY_RESIDUAL */
 } lbm_request;
 
 enum { LBM_REQ_QUEUED = 0, LBM_REQ_RUNNING = 1, LBM_REQ_CONVERGED = 2, LBM_REQ_CAPPED = 3,

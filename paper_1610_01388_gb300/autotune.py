@@ -91,6 +91,8 @@ def load(cache):
     """Apply cached decisions for this GPU; returns how many were applied."""
     n = 0
     for key, v in _read(cache).get(_gpu_name(), {}).items():
+        if key == "batch":
+            continue
         lat, model, storage, cls = key.split("/")
         lbm.lbm_tuning_set_shape(lat, model, storage, int(cls), int(v["block"]),
                                  int(v.get("cells_per_thread", 1)))
@@ -101,6 +103,8 @@ def load(cache):
 # --- batch schedule -------------------------------------------------------------
 
 BATCH_CTAS = (0, 1, 2, 4, 8)
+# plain-step tile shapes (threads per CTA, cells per thread), the default first
+BATCH_TILES = ((256, 1), (128, 1), (512, 1), (128, 2), (256, 2))
 
 
 def measure_batch(mix, steps=160, warmup=32, budget=64 << 30):
@@ -120,12 +124,20 @@ def measure_batch(mix, steps=160, warmup=32, budget=64 << 30):
     return dt
 
 
-def tune_batch(mix, steps=160):
+def _group_key(lat, prm):
+    return (lat, prm.get("model", "IR"), prm.get("storage", "F32"))
+
+
+def tune_batch(mix, steps=160, cache=None):
     """Coordinate search over the batch schedule on `mix`: group concurrency
     first (with one CTA per tile), then, group by group, the CTAs per SM of a
-    persistent grid.  Leaves the fastest schedule set; returns it with the
-    measured seconds per step of every candidate tried."""
-    keys = sorted({(lat, prm.get("model", "IR"), prm.get("storage", "F32")) for lat, _, prm in mix})
+    persistent grid, then the plain-step tile shape (threads per CTA x cells
+    per thread) for the group's size class (floor(log2) of its domains' mean
+    cell count).  Leaves the fastest schedule set; returns it with the
+    measured seconds per step of every candidate tried, and records the
+    choices in the JSON file `cache` under the GPU's name and
+    "lattice/model/storage/size class" keys (``load_batch`` applies them)."""
+    keys = sorted({_group_key(lat, prm) for lat, _, prm in mix})
     for lat, model, storage in keys:
         lbm.lbm_tuning_set_batch(lat, model, storage, 0)
     lbm.lbm_tuning_set_batch_concurrency(False)
@@ -146,5 +158,48 @@ def tune_batch(mix, steps=160):
             if t < best:
                 best, ctas[key] = t, c
         lbm.lbm_tuning_set_batch(*key, ctas[key])
+    tiles = {}
+    for key in keys:
+        lat, model, storage = key
+        sizes = [mask.size for l, mask, prm in mix if _group_key(l, prm) == key]
+        _, _, cls = lbm.lbm_tuning_get_batch_tile(lat, model, storage, sum(sizes) // len(sizes))
+        shape = BATCH_TILES[0]
+        if storage != "F64":
+            for cand in BATCH_TILES[1:]:
+                lbm.lbm_tuning_set_batch_tile(lat, model, storage, cls, *cand)
+                t = measure_batch(mix, steps)
+                tried[f"{'/'.join(key)}:tile{cand[0]}x{cand[1]}"] = t
+                if t < best:
+                    best, shape = t, cand
+        lbm.lbm_tuning_set_batch_tile(lat, model, storage, cls, *shape)
+        tiles[key] = (shape, cls)
+    if cache:
+        data = _read(cache)
+        ent = data.setdefault(_gpu_name(), {}).setdefault("batch", {})
+        ent["concurrent"] = bool(concurrent)
+        for key in keys:
+            (th, cpt), cls = tiles[key]
+            ent[f"{'/'.join(key)}/{cls}"] = {"ctas_per_sm": ctas[key], "threads": th,
+                                             "cells_per_thread": cpt}
+        with open(cache, "w") as fh:
+            json.dump(data, fh, indent=1, sort_keys=True)
     return {"concurrent": concurrent, "ctas_per_sm": {"/".join(k): v for k, v in ctas.items()},
+            "tile": {f"{'/'.join(k)}/{cls}": f"{th}x{cpt}" for k, ((th, cpt), cls) in tiles.items()},
             "seconds_per_step": best, "tried": tried}
+
+
+def load_batch(cache):
+    """Apply cached batch schedules for this GPU; returns how many group
+    entries were applied."""
+    ent = _read(cache).get(_gpu_name(), {}).get("batch", {})
+    n = 0
+    for key, v in ent.items():
+        if key == "concurrent":
+            lbm.lbm_tuning_set_batch_concurrency(bool(v))
+            continue
+        lat, model, storage, cls = key.split("/")
+        lbm.lbm_tuning_set_batch(lat, model, storage, int(v["ctas_per_sm"]))
+        lbm.lbm_tuning_set_batch_tile(lat, model, storage, int(cls), int(v["threads"]),
+                                      int(v["cells_per_thread"]))
+        n += 1
+    return n

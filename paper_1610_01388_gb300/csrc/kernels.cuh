@@ -783,22 +783,27 @@ __device__ __forceinline__ void block_sum_store(V (&v)[kNumStats], double* __res
 // the fused step
 //
 // Minimum resident blocks per SM requested from the register allocator (0 =
-// let it choose).  PR in FP32 arithmetic: 9 blocks of 128 threads (at most 56
-// registers, 36 warps) measured best on GB300 (a tighter cap spills); 256 and
-// 512 threads keep the 64-register cap they reach anyway.  IR (48 registers)
-// and FP64 arithmetic (which these caps would make spill) are left to the
-// allocator.  BLBM_PR_MINB / BLBM_IR_MINB override at build time.
+// let it choose).  PR in FP32 arithmetic (FP32 and 16-bit storage): D3Q27
+// keeps 1024 threads resident per SM at 256 and 512 threads per block (64
+// registers) and 9 blocks at 128 (56 registers); a tighter cap spills.  The
+// smaller lattices keep 1280 (10 x 128, 5 x 256, 2 x 512): D3Q19 PR then
+// takes 48 registers without spilling and measured 7-9 % faster than at 64
+// (porous box 256^3: FP32 466 -> 430 us, FP16 440 -> 401 us; duct
+// 256 x 128 x 128: FP32 113.5 -> 105.7 us).  IR (40-48 registers) and FP64
+// arithmetic (which these caps would make spill) are left to the allocator.
+// BLBM_PR_MINB / BLBM_IR_MINB override at build time.
 #ifndef BLBM_PR_MINB
 #define BLBM_PR_MINB -1
 #endif
 #ifndef BLBM_IR_MINB
 #define BLBM_IR_MINB 0
 #endif
-template <int MODEL, class S, int BLOCK> constexpr int step_min_blocks() {
+template <class L, int MODEL, class S, bool CHECK, int BLOCK> constexpr int step_min_blocks() {
     if (MODEL == LBM_MODEL_IR) return BLBM_IR_MINB;
     if (std::is_same<typename Store<S>::R, double>::value) return 0;
     if (BLBM_PR_MINB >= 0) return BLBM_PR_MINB;
-    return BLOCK == 128 ? 9 : 1024 / BLOCK;
+    if (L::Q == 27 || CHECK) return BLOCK == 128 ? 9 : 1024 / BLOCK;   // check steps: no spill
+    return 1280 / BLOCK;
 }
 
 // One cell of one time step: pull, collide, store; on check steps the cell's
@@ -861,19 +866,26 @@ __device__ __forceinline__ void cell_step(const KParams& kp, const Coef<typename
     }
 }
 
-// Plain steps in which solid cells of warps holding fluid cells copy their
-// populations through (cell_step, fluid = false).  The PR step of the 16-bit
-// forms is left out: there the copy path's registers cost more spills on the
-// duct (about 6 %) than the whole sectors gain in porous media (about 6 %).
-template <int MODEL, class S> __host__ __device__ constexpr bool copy_through() {
-    return !(MODEL != LBM_MODEL_IR && sizeof(S) == 2);
+// Copy-through: the solid cells of a warp that holds fluid cells run
+// cell_step with fluid = false, which stores their populations unchanged, so
+// the warp's stores fill whole sectors (plain and check steps).  For the PR
+// step of the 16-bit forms it is a per-solver choice (COPY), because there
+// its path costs registers: on the D3Q27 duct, which has no warp mixing
+// solid and fluid cells, it spills and the step is 6 % slower, while on a
+// porous box it saves 7 % (256^3 D3Q19: 431 -> 401 us).  The solver takes it
+// when at least 1 % of its warps with fluid cells also hold solid ones.
+// (Solid lanes copying their raw words in a branch of their own keep the
+// fluid path's registers, but a mixed warp then runs both branches one after
+// the other: 40 % slower on the porous box in FP32.)
+template <int MODEL, class S> __host__ __device__ constexpr bool copy_is_choice() {
+    return MODEL != LBM_MODEL_IR && sizeof(S) == 2;
 }
 
 // BLOCK: threads per block, chosen per (lattice, model, storage, size class)
 // by the tuning table; check steps always run with kBlock so their reduction
 // order does not depend on the tuning.
-template <class L, int MODEL, class S, bool CHECK, int BLOCK = kBlock>
-__global__ void __launch_bounds__(BLOCK, step_min_blocks<MODEL, S, BLOCK>())
+template <class L, int MODEL, class S, bool CHECK, int BLOCK = kBlock, bool COPY = true>
+__global__ void __launch_bounds__(BLOCK, step_min_blocks<L, MODEL, S, CHECK, BLOCK>())
 k_step(const KArgs a, const SrcPlanes<S> src, const DstPlanes<S> dst,
        const uint32_t* __restrict__ links, typename Store<S>::R* __restrict__ tau,
        typename Store<S>::R* __restrict__ usnap, double* __restrict__ partials,
@@ -888,13 +900,13 @@ k_step(const KArgs a, const SrcPlanes<S> src, const DstPlanes<S> dst,
         // this launch reads counter[parity] and leaves counter + 1 for the next
         const uint32_t seed = __ldg(rng_ctr + parity);
         if (blockIdx.x == 0 && threadIdx.x == 0) rng_ctr[parity ^ 1] = seed + 1u;
-        rnd = pcg_hash((uint32_t)idx ^ (seed * 0x9e3779b9u));
+        rnd = pcg_hash(((uint32_t)idx + kp.hash_offset) ^ (seed * 0x9e3779b9u));
     }
     const uint32_t lk = inside ? __ldg(links + idx) : kSolidBit;
     const bool active = !(lk & kSolidBit);
     R acc[kNumStats];
     if constexpr (!CHECK) {
-        if constexpr (copy_through<MODEL, S>()) {
+        if constexpr (COPY) {
             // a warp without fluid cells has nothing to do; in any other warp
             // the solid cells inside the domain copy their populations through
             if (!__any_sync(__activemask(), active) || !inside) return;
@@ -907,7 +919,16 @@ k_step(const KArgs a, const SrcPlanes<S> src, const DstPlanes<S> dst,
     } else {
 #pragma unroll
         for (int k = 0; k < kNumStats; ++k) acc[k] = R(0);
-        if (active) cell_step<L, MODEL, S, true>(kp, coef<R>(a), src, dst, lk, idx, tau, usnap, rnd, acc);
+        if constexpr (COPY) {
+            // solid cells add nothing to the sums: their velocity and snapshot are 0
+            const bool warp_fluid = __any_sync(__activemask(), active);
+            if (warp_fluid && inside)
+                cell_step<L, MODEL, S, true>(kp, coef<R>(a), src, dst, lk, idx, tau, usnap, rnd, acc,
+                                             active);
+        } else {
+            if (active)
+                cell_step<L, MODEL, S, true>(kp, coef<R>(a), src, dst, lk, idx, tau, usnap, rnd, acc);
+        }
         block_sum_store(acc, partials + (int64_t)blockIdx.x * kNumStats);
     }
 }
@@ -987,8 +1008,8 @@ k_step2(const KArgs a, const SrcPlanes<S> src, const DstPlanes<S> dst,
     const bool act[2] = {a0, a1};
     uint32_t rnd[2] = {0u, 0u};
     if constexpr (Store<S>::kStochastic) {
-        rnd[0] = pcg_hash((uint32_t)idx[0] ^ (seed * 0x9e3779b9u));
-        rnd[1] = pcg_hash((uint32_t)idx[1] ^ (seed * 0x9e3779b9u));
+        rnd[0] = pcg_hash(((uint32_t)idx[0] + kp.hash_offset) ^ (seed * 0x9e3779b9u));
+        rnd[1] = pcg_hash(((uint32_t)idx[1] + kp.hash_offset) ^ (seed * 0x9e3779b9u));
     }
     cell_step2<L, MODEL, S>(kp, a.cf, src, dst, lk, idx, act, tau, rnd);
 }
@@ -1009,19 +1030,22 @@ struct BatchDesc {
     void* usnap;
     uint32_t* rng;      // two launch counters (16-bit storage)
     int parity0;
-    int block_begin;
-    int nblocks;
+    int block_begin;    // first 256-cell tile of this domain (check steps)
+    int nblocks;        // its 256-cell tiles
     int slot;           // row of this domain in the batch's per-domain stats
+    int pblock_begin;   // first tile of this domain in the plain-step tile map
 };
 
 template <class R> __device__ __forceinline__ const Coef<R>& bcoef(const BatchDesc& d);
 template <> __device__ __forceinline__ const Coef<float>& bcoef<float>(const BatchDesc& d) { return d.cf; }
 template <> __device__ __forceinline__ const Coef<double>& bcoef<double>(const BatchDesc& d) { return d.cd; }
 
-// One batch step of one tile (kBlock consecutive cells of one domain).
-template <class L, int MODEL, class S, bool CHECK>
-__device__ __forceinline__ void batch_tile(const BatchDesc& D, int tile, int phase,
-                                           double* __restrict__ partials) {
+// One check step of one tile (kBlock consecutive cells of one domain): as
+// k_step's check step, with the copy-through for every form (the solid cells
+// of a warp with fluid cells copy their populations through).
+template <class L, int MODEL, class S>
+__device__ __forceinline__ void batch_tile_check(const BatchDesc& D, int tile, int phase,
+                                                 double* __restrict__ partials) {
     using R = typename Store<S>::R;
     const KParams& kp = D.kp;
     const int lb = tile - D.block_begin;
@@ -1035,46 +1059,69 @@ __device__ __forceinline__ void batch_tile(const BatchDesc& D, int tile, int pha
         // reads counter[cur], leaves counter + 1 in the other slot for the next launch
         const uint32_t seed = D.rng[cur];
         if (lb == 0 && threadIdx.x == 0) D.rng[cur ^ 1] = seed + 1u;
-        rnd = pcg_hash((uint32_t)idx ^ (seed * 0x9e3779b9u));
+        rnd = pcg_hash(((uint32_t)idx + kp.hash_offset) ^ (seed * 0x9e3779b9u));
     }
     const uint32_t lk = inside ? __ldg(D.links + idx) : kSolidBit;
     const bool active = !(lk & kSolidBit);
+    const bool warp_fluid = __any_sync(__activemask(), active);
     R acc[kNumStats];
-    if constexpr (!CHECK) {
-        // as in k_step: solid cells of a warp with fluid cells copy through
-        if constexpr (copy_through<MODEL, S>()) {
-            if (!__any_sync(__activemask(), active) || !inside) return;
+#pragma unroll
+    for (int k = 0; k < kNumStats; ++k) acc[k] = R(0);
+    if (warp_fluid && inside)
+        cell_step<L, MODEL, S, true>(kp, bcoef<R>(D), src, dst, lk, idx, (R*)D.tau, (R*)D.usnap,
+                                     rnd, acc, active);
+    block_sum_store(acc, partials + (int64_t)tile * kNumStats);
+}
+
+// One plain step of one tile of T x C cells of one domain (the tile shape the
+// batch schedule sets per group): thread t steps cells base + t, base + t + T,
+// ... (C of them, one after the other), so every warp access stays
+// contiguous.  Per cell as k_step, with the copy-through for every form.
+template <class L, int MODEL, class S, int T, int C>
+__device__ __forceinline__ void batch_tile_plain(const BatchDesc& D, int tile, int phase) {
+    using R = typename Store<S>::R;
+    const KParams& kp = D.kp;
+    const int lb = tile - D.pblock_begin;
+    const int cur = phase ^ D.parity0;
+    const SrcStride<S> src{(const S*)D.f[cur], (int)kp.plane};
+    const DstStride<S> dst{(S*)D.f[cur ^ 1], (int)kp.plane};
+    uint32_t seed = 0u;
+    if constexpr (Store<S>::kStochastic) {
+        // reads counter[cur], leaves counter + 1 in the other slot for the next launch
+        seed = D.rng[cur];
+        if (lb == 0 && threadIdx.x == 0) D.rng[cur ^ 1] = seed + 1u;
+    }
+#pragma unroll 1
+    for (int c = 0; c < C; ++c) {
+        const int idx = (lb * C + c) * T + (int)threadIdx.x;
+        const bool inside = idx < kp.ncells;
+        uint32_t rnd = 0u;
+        if constexpr (Store<S>::kStochastic) rnd = pcg_hash(((uint32_t)idx + kp.hash_offset) ^ (seed * 0x9e3779b9u));
+        const uint32_t lk = inside ? __ldg(D.links + idx) : kSolidBit;
+        const bool active = !(lk & kSolidBit);
+        const bool warp_fluid = __any_sync(__activemask(), active);
+        R acc[kNumStats];
+        if (warp_fluid && inside)
             cell_step<L, MODEL, S, false>(kp, bcoef<R>(D), src, dst, lk, idx, (R*)D.tau,
                                           (R*)D.usnap, rnd, acc, active);
-        } else {
-            if (!active) return;
-            cell_step<L, MODEL, S, false>(kp, bcoef<R>(D), src, dst, lk, idx, (R*)D.tau,
-                                          (R*)D.usnap, rnd, acc);
-        }
-    } else {
-#pragma unroll
-        for (int k = 0; k < kNumStats; ++k) acc[k] = R(0);
-        if (active)
-            cell_step<L, MODEL, S, true>(kp, bcoef<R>(D), src, dst, lk, idx, (R*)D.tau,
-                                         (R*)D.usnap, rnd, acc);
-        block_sum_store(acc, partials + (int64_t)tile * kNumStats);
     }
 }
 
-// Batch step: the CTAs walk the tiles of every domain of the group (tile t,
+// Batch steps: the CTAs walk the tiles of every domain of the group (tile t,
 // t + gridDim.x, ...).  With one CTA per tile this is the plain launch; with
-// fewer CTAs it is a persistent grid.  Partials are indexed by tile, so check
-// steps reduce in the same order for every grid size.
-// Register budget of the batch kernel: plain PR steps in FP32 arithmetic keep
-// 4 resident 256-thread blocks (64 registers).  Without it the 16-bit forms
-// take 72 registers and FP32 storage 70 (the descriptor's coefficients are
-// loaded, not kernel-parameter operands), leaving 3 blocks; on a single
-// D3Q27 duct the FP32 PR batch step measured 170 us without and 154 us with
-// the budget.  Plain IR steps of the 16-bit forms keep 5 blocks (48
-// registers; their copy-through path takes 58 and 4 blocks otherwise).  FP32
-// IR, check steps and FP64 are left to the allocator.  BLBM_BATCH_PR_MINB
-// (16-bit PR), BLBM_BATCH_PR32_MINB (FP32 PR) and BLBM_BATCH_IR16_MINB
-// override at build time.
+// fewer CTAs it is a persistent grid.  Check-step partials are indexed by
+// 256-cell tile, so check steps reduce in the same order for every grid size
+// and every plain-step tile shape.
+// Register budget of the batch kernels, as resident 256-thread blocks (scaled
+// to the tile's threads): plain PR steps in FP32 arithmetic keep 4 (64
+// registers).  Without it the 16-bit forms take 72 registers and FP32
+// storage 70 (the descriptor's coefficients are loaded, not kernel-parameter
+// operands), leaving 3 blocks; on a single D3Q27 duct the FP32 PR batch step
+// measured 170 us without and 154 us with the budget.  Plain IR steps of the
+// 16-bit forms keep 5 (48 registers; their copy-through path takes 58 and 4
+// blocks otherwise).  FP32 IR, check steps and FP64 are left to the
+// allocator.  BLBM_BATCH_PR_MINB (16-bit PR), BLBM_BATCH_PR32_MINB (FP32 PR)
+// and BLBM_BATCH_IR16_MINB override at build time.
 #ifndef BLBM_BATCH_PR_MINB
 #define BLBM_BATCH_PR_MINB 4
 #endif
@@ -1091,14 +1138,22 @@ template <int MODEL, class S, bool CHECK> constexpr int batch_min_blocks() {
          : sizeof(S) == 4 ? BLBM_BATCH_PR32_MINB : 0;
 }
 
-template <class L, int MODEL, class S, bool CHECK>
-__global__ void __launch_bounds__(kBlock, batch_min_blocks<MODEL, S, CHECK>())
-k_step_batch(const BatchDesc* __restrict__ descs, const int* __restrict__ block_dom, int ntiles,
-             int phase, double* __restrict__ partials) {
+template <class L, int MODEL, class S>
+__global__ void __launch_bounds__(kBlock)
+k_step_batch_check(const BatchDesc* __restrict__ descs, const int* __restrict__ block_dom,
+                   int ntiles, int phase, double* __restrict__ partials) {
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        batch_tile<L, MODEL, S, CHECK>(descs[block_dom[t]], t, phase, partials);
-        if constexpr (CHECK) __syncthreads();   // block_sum_store's shared rows are reused
+        batch_tile_check<L, MODEL, S>(descs[block_dom[t]], t, phase, partials);
+        __syncthreads();   // block_sum_store's shared rows are reused
     }
+}
+
+template <class L, int MODEL, class S, int T, int C>
+__global__ void __launch_bounds__(T, batch_min_blocks<MODEL, S, false>() * kBlock / T)
+k_step_batch(const BatchDesc* __restrict__ descs, const int* __restrict__ tile_dom, int ntiles,
+             int phase) {
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x)
+        batch_tile_plain<L, MODEL, S, T, C>(descs[tile_dom[t]], t, phase);
 }
 
 // macroscopic fields of the streamed populations
@@ -1174,18 +1229,22 @@ k_reduce(const KArgs a, const SrcPlanes<S> f, const uint32_t* __restrict__ links
 }
 
 // solid / bounce-back link bits: bit i set if the cell at x - c_i is solid
+// (With LBM_FLAG_Z_GHOSTS the first and last z-planes are ghost planes: they
+// are never stepped, like solid cells, while their mask rows, the
+// neighbouring slabs' own, still set the link bits of the planes next to them.)
 template <class L>
 __global__ void __launch_bounds__(kBlock)
 k_links(const KParams kp, const uint8_t* __restrict__ mask, uint32_t* __restrict__ links) {
     const int idx = blockIdx.x * kBlock + threadIdx.x;
     if (idx >= kp.ncells) return;
-    if (mask[idx]) {
-        links[idx] = kSolidBit;
-        return;
-    }
     const int nx = kp.nx, ny = kp.ny, nz = kp.nz;
     int x, y, z;
     cell_xyz(kp, idx, x, y, z);
+    const bool ghost = (kp.flags & LBM_FLAG_Z_GHOSTS) && (z == 0 || z == nz - 1);
+    if (mask[idx] || ghost) {
+        links[idx] = kSolidBit;
+        return;
+    }
     uint32_t bits = 0;
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
@@ -1212,6 +1271,45 @@ k_convert(const KParams kp, int q, bool to_device, S* __restrict__ f, double* __
         *p = Store<S>::enc(buf[idx] - w, w);
     else
         buf[idx] = Store<S>::dec(*p, w) + w;
+}
+
+// Slab faces (LBM_FLAG_Z_GHOSTS).  The populations that cross a z-face are
+// those with c_z = +1 (moving up) and c_z = -1 (moving down).  side 1 packs
+// the last interior plane's c_z = +1 populations (the upper neighbour's lower
+// ghost plane receives them: its side 0 unpack); side 0 packs the first
+// interior plane's c_z = -1 populations (the lower neighbour's side 1
+// unpack, into its upper ghost plane).  buf holds the stored values (no
+// conversion), [j][cell of the plane] for the j-th crossing population in the
+// lattice's order.
+template <class L> __host__ __device__ constexpr int face_count() {
+    int n = 0;
+    for (int i = 0; i < L::Q; ++i) n += L::cz(i) == 1;
+    return n;
+}
+template <class L> __device__ __forceinline__ int face_pop(int j, int cz) {
+    int n = 0;
+    for (int i = 0; i < L::Q; ++i)
+        if (L::cz(i) == cz && n++ == j) return i;
+    return -1;
+}
+
+template <class L, class S>
+__global__ void __launch_bounds__(kBlock)
+k_halo(const KParams kp, S* __restrict__ f, S* __restrict__ buf, int side, bool pack) {
+    const int nxy = kp.nx * kp.ny;
+    const int k = blockIdx.x * kBlock + threadIdx.x;
+    if (k >= face_count<L>() * nxy) return;
+    const int j = k / nxy, xy = k - j * nxy;
+    // pack: interior plane next to the face, populations leaving through it;
+    // unpack: ghost plane of the face, populations entering through it
+    const int cz = (side == 1) == pack ? 1 : -1;
+    const int z = pack ? (side == 1 ? kp.nz - 2 : 1) : (side == 1 ? kp.nz - 1 : 0);
+    const int i = face_pop<L>(j, cz);
+    S* p = f + pop_base<S>(i, kp.plane) + (int64_t)pop_step<S>(i) * ((int64_t)z * nxy + xy);
+    if (pack)
+        buf[k] = *p;
+    else
+        *p = buf[k];
 }
 
 // full FP64 populations of listed cells: out[i * n + k] = f_i(cells[k])
@@ -1297,8 +1395,8 @@ template <class L, class S> inline DstPlanes<S> dst_planes(void* f, int64_t plan
     return P;
 }
 
-template <class L, int MODEL, class S>
-cudaError_t launch_step_t(bool check, const KParams& kp, const StepArgs& s, cudaStream_t st) {
+template <class L, int MODEL, class S, bool COPY>
+cudaError_t launch_step_c(bool check, const KParams& kp, const StepArgs& s, cudaStream_t st) {
     using R = typename Store<S>::R;
     const KArgs a = make_args<L>(kp);
     const int grid = step_grid(kp.ncells);
@@ -1317,24 +1415,34 @@ cudaError_t launch_step_t(bool check, const KParams& kp, const StepArgs& s, cuda
         }
     }
     if (check) {
-        k_step<L, MODEL, S, true><<<grid, kBlock, 0, st>>>(
+        k_step<L, MODEL, S, true, kBlock, COPY><<<grid, kBlock, 0, st>>>(
             a, src, dst, s.links, (R*)s.tau, (R*)s.usnap, s.partials, s.rng_ctr, s.parity);
     } else if constexpr (MODEL != kModelPRImplicit) {
         if (block == 128) {
-            k_step<L, MODEL, S, false, 128><<<(kp.ncells + 127) / 128, 128, 0, st>>>(
+            k_step<L, MODEL, S, false, 128, COPY><<<(kp.ncells + 127) / 128, 128, 0, st>>>(
                 a, src, dst, s.links, (R*)s.tau, (R*)s.usnap, s.partials, s.rng_ctr, s.parity);
         } else if (block == 512) {
-            k_step<L, MODEL, S, false, 512><<<(kp.ncells + 511) / 512, 512, 0, st>>>(
+            k_step<L, MODEL, S, false, 512, COPY><<<(kp.ncells + 511) / 512, 512, 0, st>>>(
                 a, src, dst, s.links, (R*)s.tau, (R*)s.usnap, s.partials, s.rng_ctr, s.parity);
         } else {
-            k_step<L, MODEL, S, false><<<grid, kBlock, 0, st>>>(
+            k_step<L, MODEL, S, false, kBlock, COPY><<<grid, kBlock, 0, st>>>(
                 a, src, dst, s.links, (R*)s.tau, (R*)s.usnap, s.partials, s.rng_ctr, s.parity);
         }
     } else {
-        k_step<L, MODEL, S, false><<<grid, kBlock, 0, st>>>(
+        k_step<L, MODEL, S, false, kBlock, COPY><<<grid, kBlock, 0, st>>>(
             a, src, dst, s.links, (R*)s.tau, (R*)s.usnap, s.partials, s.rng_ctr, s.parity);
     }
     return cudaGetLastError();
+}
+
+// The copy-through is on for every form but the PR step of the 16-bit ones,
+// which follows the solver's geometry (s.copy).
+template <class L, int MODEL, class S>
+cudaError_t launch_step_t(bool check, const KParams& kp, const StepArgs& s, cudaStream_t st) {
+    if constexpr (copy_is_choice<MODEL, S>()) {
+        if (!s.copy) return launch_step_c<L, MODEL, S, false>(check, kp, s, st);
+    }
+    return launch_step_c<L, MODEL, S, true>(check, kp, s, st);
 }
 
 template <class L, class S>
@@ -1357,35 +1465,57 @@ cudaError_t launch_step_lat(int model, int storage, bool check, const KParams& k
     }
 }
 
+// Plain-step tile shapes of the batch (threads per CTA x cells per thread);
+// FP64 storage and the Newton-implicit PR step run 256 x 1 only.
+template <int MODEL, class S> constexpr bool batch_shapes_all() {
+    return MODEL != kModelPRImplicit && !std::is_same<S, double>::value;
+}
+
 template <class L, int MODEL, class S>
 cudaError_t launch_batch_t(bool check, const BatchDesc* descs, const int* block_dom, int nblocks,
-                           int grid, int phase, double* partials, cudaStream_t st) {
-    if (check)
-        k_step_batch<L, MODEL, S, true><<<grid, kBlock, 0, st>>>(descs, block_dom, nblocks, phase, partials);
-    else
-        k_step_batch<L, MODEL, S, false><<<grid, kBlock, 0, st>>>(descs, block_dom, nblocks, phase, partials);
+                           int grid, int phase, double* partials, int threads, int cpt,
+                           cudaStream_t st) {
+    if (check) {
+        k_step_batch_check<L, MODEL, S><<<grid, kBlock, 0, st>>>(descs, block_dom, nblocks, phase, partials);
+    } else if (threads == 256 && cpt == 1) {
+        k_step_batch<L, MODEL, S, 256, 1><<<grid, 256, 0, st>>>(descs, block_dom, nblocks, phase);
+    } else if constexpr (batch_shapes_all<MODEL, S>()) {
+        if (threads == 128 && cpt == 1)
+            k_step_batch<L, MODEL, S, 128, 1><<<grid, 128, 0, st>>>(descs, block_dom, nblocks, phase);
+        else if (threads == 512 && cpt == 1)
+            k_step_batch<L, MODEL, S, 512, 1><<<grid, 512, 0, st>>>(descs, block_dom, nblocks, phase);
+        else if (threads == 128 && cpt == 2)
+            k_step_batch<L, MODEL, S, 128, 2><<<grid, 128, 0, st>>>(descs, block_dom, nblocks, phase);
+        else if (threads == 256 && cpt == 2)
+            k_step_batch<L, MODEL, S, 256, 2><<<grid, 256, 0, st>>>(descs, block_dom, nblocks, phase);
+        else
+            return cudaErrorInvalidValue;
+    } else {
+        return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 
 template <class L, class S>
 cudaError_t launch_batch_model(int model, bool check, const BatchDesc* descs, const int* block_dom,
-                               int nblocks, int grid, int phase, double* partials, cudaStream_t st) {
+                               int nblocks, int grid, int phase, double* partials, int threads,
+                               int cpt, cudaStream_t st) {
     if (model == kModelPRImplicit)
-        return launch_batch_t<L, kModelPRImplicit, S>(check, descs, block_dom, nblocks, grid, phase, partials, st);
+        return launch_batch_t<L, kModelPRImplicit, S>(check, descs, block_dom, nblocks, grid, phase, partials, threads, cpt, st);
     if (model == LBM_MODEL_PR)
-        return launch_batch_t<L, LBM_MODEL_PR, S>(check, descs, block_dom, nblocks, grid, phase, partials, st);
-    return launch_batch_t<L, LBM_MODEL_IR, S>(check, descs, block_dom, nblocks, grid, phase, partials, st);
+        return launch_batch_t<L, LBM_MODEL_PR, S>(check, descs, block_dom, nblocks, grid, phase, partials, threads, cpt, st);
+    return launch_batch_t<L, LBM_MODEL_IR, S>(check, descs, block_dom, nblocks, grid, phase, partials, threads, cpt, st);
 }
 
 template <class L>
 cudaError_t launch_batch_lat(int model, int storage, bool check, const BatchDesc* descs,
                              const int* block_dom, int nblocks, int grid, int phase,
-                             double* partials, cudaStream_t st) {
+                             double* partials, int threads, int cpt, cudaStream_t st) {
     switch (storage) {
-    case LBM_F32: return launch_batch_model<L, float>(model, check, descs, block_dom, nblocks, grid, phase, partials, st);
-    case LBM_F64: return launch_batch_model<L, double>(model, check, descs, block_dom, nblocks, grid, phase, partials, st);
-    case LBM_F16_OFS: return launch_batch_model<L, __half>(model, check, descs, block_dom, nblocks, grid, phase, partials, st);
-    case LBM_BF16_OFS: return launch_batch_model<L, __nv_bfloat16>(model, check, descs, block_dom, nblocks, grid, phase, partials, st);
+    case LBM_F32: return launch_batch_model<L, float>(model, check, descs, block_dom, nblocks, grid, phase, partials, threads, cpt, st);
+    case LBM_F64: return launch_batch_model<L, double>(model, check, descs, block_dom, nblocks, grid, phase, partials, threads, cpt, st);
+    case LBM_F16_OFS: return launch_batch_model<L, __half>(model, check, descs, block_dom, nblocks, grid, phase, partials, threads, cpt, st);
+    case LBM_BF16_OFS: return launch_batch_model<L, __nv_bfloat16>(model, check, descs, block_dom, nblocks, grid, phase, partials, threads, cpt, st);
     default: return cudaErrorNotSupported;
     }
 }
@@ -1473,6 +1603,23 @@ cudaError_t launch_gather_lat(int storage, const KParams& kp, const void* f, con
     return cudaGetLastError();
 }
 
+template <class L>
+cudaError_t launch_halo_lat(int storage, const KParams& kp, void* f, void* buf, int side,
+                            bool pack, cudaStream_t st) {
+    const int n = face_count<L>() * kp.nx * kp.ny;
+    const int grid = (n + kBlock - 1) / kBlock;
+    switch (storage) {
+    case LBM_F32: k_halo<L, float><<<grid, kBlock, 0, st>>>(kp, (float*)f, (float*)buf, side, pack); break;
+    case LBM_F64: k_halo<L, double><<<grid, kBlock, 0, st>>>(kp, (double*)f, (double*)buf, side, pack); break;
+    case LBM_F16_OFS: k_halo<L, __half><<<grid, kBlock, 0, st>>>(kp, (__half*)f, (__half*)buf, side, pack); break;
+    case LBM_BF16_OFS: k_halo<L, __nv_bfloat16><<<grid, kBlock, 0, st>>>(kp, (__nv_bfloat16*)f, (__nv_bfloat16*)buf, side, pack); break;
+    default: return cudaErrorNotSupported;
+    }
+    return cudaGetLastError();
+}
+
+template <class L> int face_count_lat() { return face_count<L>(); }
+
 template <class L> void lattice_table(int* c, double* w) {
     for (int i = 0; i < L::Q; ++i) {
         if (c) {
@@ -1515,10 +1662,20 @@ template <class L> void lattice_table(int* c, double* w) {
                                   const int64_t* cells, int n, double* out, cudaStream_t st) {  \
         return launch_gather_lat<L>(storage, kp, f, cells, n, out, st);                         \
     }                                                                                           \
+    cudaError_t launch_halo_##L(int storage, const KParams& kp, void* f, void* buf, int side,  \
+                                bool pack, cudaStream_t st) {                                   \
+        return launch_halo_lat<L>(storage, kp, f, buf, side, pack, st);                         \
+    }                                                                                           \
+    int face_count_##L() { return face_count_lat<L>(); }                                        \
+    }
+
+// The batch kernels of a lattice, in a translation unit of their own.
+#define BLBM_DEFINE_BATCH_LAUNCHERS(L)                                                         \
+    namespace blbm {                                                                            \
     cudaError_t launch_step_batch_##L(int model, int storage, bool check, const BatchDesc* descs,\
                                       const int* block_dom, int nblocks, int grid, int phase,  \
-                                      double* partials, cudaStream_t st) {                      \
+                                      double* partials, int threads, int cpt, cudaStream_t st) {\
         return launch_batch_lat<L>(model, storage, check, descs, block_dom, nblocks, grid,      \
-                                   phase, partials, st);                                        \
+                                   phase, partials, threads, cpt, st);                          \
     }                                                                                           \
     }

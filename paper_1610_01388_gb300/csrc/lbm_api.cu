@@ -11,6 +11,7 @@
 //   stats     finalised reduction results, then two u32 launch counters
 //             (stochastic rounding of the 16-bit storage forms)
 //   mask      the uploaded solid mask (bytes)
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -113,13 +114,18 @@ lbm_status validate(int lat, int nx, int ny, int nz, const uint8_t* mask, const 
         if (!std::isfinite(p->g[d])) return fail(LBM_EINVAL, "g must be finite");
     if (lat == LBM_D2Q9 && p->g[2] != 0.0) return fail(LBM_EINVAL, "D2Q9 needs g[2] == 0");
     if (p->check_every < 0) return fail(LBM_EINVAL, "check_every must be >= 0");
-    if (p->flags & ~LBM_FLAG_BURNETT_X) return fail(LBM_EINVAL, "unknown flags 0x%x", p->flags);
+    if (p->flags & ~(LBM_FLAG_BURNETT_X | LBM_FLAG_Z_GHOSTS))
+        return fail(LBM_EINVAL, "unknown flags 0x%x", p->flags);
+    if ((p->flags & LBM_FLAG_Z_GHOSTS) && (lat == LBM_D2Q9 || nz < 3))
+        return fail(LBM_EINVAL, "ghost planes need a 3D lattice and nz >= 3 (got nz = %d)", nz);
     if (p->newton_iters < 0 || p->newton_iters > 64)
         return fail(LBM_EINVAL, "newton_iters must be in 0..64 (got %d)", p->newton_iters);
     if (p->reserved != 0) return fail(LBM_EINVAL, "reserved must be 0");
     if (!mask) return fail(LBM_EINVAL, "solid_mask is NULL");
     int64_t fluid = 0;
-    for (int64_t i = 0; i < n; ++i) fluid += mask[i] == 0;
+    const int64_t plane = (int64_t)nx * ny;
+    const bool ghosts = (p->flags & LBM_FLAG_Z_GHOSTS) != 0;
+    for (int64_t i = ghosts ? plane : 0; i < (ghosts ? n - plane : n); ++i) fluid += mask[i] == 0;
     if (fluid == 0) return fail(LBM_EINVAL, "the mask has no fluid cell");
     return LBM_OK;
 }
@@ -171,6 +177,7 @@ cudaError_t launch_step(lbm_solver* s, bool check, cudaStream_t st) {
     a.parity = s->cur;
     a.block = s->block;
     a.cpt = s->cpt;
+    a.copy = s->copy;
     const int km = kernel_model(s->p.model, s->kp.newton);
     switch (s->lat) {
     case LBM_D2Q9: return launch_step_D2Q9(km, s->p.storage, check, s->kp, a, st);
@@ -209,8 +216,8 @@ cudaError_t launch_reduce(lbm_solver* s, int mode, int nblocks) {
     }
 }
 
-cudaError_t launch_convert(lbm_solver* s, bool to_device, int q, double* buf) {
-    void* f = s->f[s->cur];
+cudaError_t launch_convert(lbm_solver* s, bool to_device, int q, double* buf, int which) {
+    void* f = s->f[which];
     switch (s->lat) {
     case LBM_D2Q9: return launch_convert_D2Q9(s->p.storage, to_device, s->kp, q, f, buf, s->stream);
     case LBM_D3Q15: return launch_convert_D3Q15(s->p.storage, to_device, s->kp, q, f, buf, s->stream);
@@ -440,7 +447,25 @@ static lbm_status create_impl(lbm_solver** out, lbm_lattice lat, int nx, int ny,
     s->ncells = nx * ny * nz;
     s->p = *p;
     s->stream = (cudaStream_t)stream;
-    for (int i = 0; i < s->ncells; ++i) s->nfluid += mask[i] == 0;
+    // fluid cells: the stepped ones (ghost planes are not)
+    const int nxy = nx * ny;
+    const bool ghosts = (p->flags & LBM_FLAG_Z_GHOSTS) != 0;
+    auto stepped = [&](int i) { return mask[i] == 0 && !(ghosts && (i < nxy || i >= s->ncells - nxy)); };
+    for (int i = 0; i < s->ncells; ++i) s->nfluid += stepped(i);
+    {
+        // warps (32 consecutive cells) holding fluid cells, and those of them
+        // that also hold solid cells: the copy-through choice of the 16-bit PR
+        // step (taken when at least 1 % of the warps with fluid are mixed)
+        int64_t with_fluid = 0, mixed = 0;
+        for (int w0 = 0; w0 < s->ncells; w0 += 32) {
+            const int w1 = std::min(w0 + 32, s->ncells);
+            int nf = 0;
+            for (int i = w0; i < w1; ++i) nf += stepped(i);
+            with_fluid += nf > 0;
+            mixed += nf > 0 && nf < w1 - w0;
+        }
+        s->copy = 100 * mixed >= with_fluid ? 1 : 0;
+    }
     s->lay = make_layout(lat, nx, ny, nz, *p);
     KParams& kp = s->kp;
     kp.nx = nx;
@@ -762,9 +787,13 @@ lbm_status lbm_set_populations(lbm_solver* s, const double* f) {
     if (!f) return fail(LBM_EINVAL, "f is NULL");
     if ((v = ensure_scratch(s)) != LBM_OK) return v;
     WAIT(s, "lbm_set_populations");
+    // both buffers: a step writes every fluid cell of the other buffer, but
+    // not every solid cell, so solid-cell populations read back later are the
+    // uploaded ones whichever buffer is current then
     for (int q = 0; q < s->Q; ++q) {
         CK(s, cudaMemcpyAsync(s->scratch, f + (size_t)q * s->ncells, (size_t)s->ncells * sizeof(double), cudaMemcpyHostToDevice, s->stream), "population upload");
-        CK(s, launch_convert(s, true, q, s->scratch), "population convert");
+        CK(s, launch_convert(s, true, q, s->scratch, s->cur), "population convert");
+        CK(s, launch_convert(s, true, q, s->scratch, s->cur ^ 1), "population convert");
     }
     CK(s, cudaStreamSynchronize(s->stream), "population sync");
     return LBM_OK;
@@ -777,7 +806,7 @@ lbm_status lbm_get_populations(lbm_solver* s, double* f) {
     if ((v = ensure_scratch(s)) != LBM_OK) return v;
     WAIT(s, "lbm_get_populations");
     for (int q = 0; q < s->Q; ++q) {
-        CK(s, launch_convert(s, false, q, s->scratch), "population convert");
+        CK(s, launch_convert(s, false, q, s->scratch, s->cur), "population convert");
         CK(s, cudaMemcpyAsync(f + (size_t)q * s->ncells, s->scratch, (size_t)s->ncells * sizeof(double), cudaMemcpyDeviceToHost, s->stream), "population download");
     }
     CK(s, cudaStreamSynchronize(s->stream), "population sync");
@@ -851,6 +880,72 @@ lbm_status lbm_get_tau(lbm_solver* s, double* tau) {
     return LBM_OK;
 }
 
+lbm_status lbm_check_sums(lbm_solver* s, double usum[3], double* du2, double* u2) {
+    lbm_status v = enter(s);
+    if (v != LBM_OK) return v;
+    WAIT(s, "lbm_check_sums");
+    const double* r = s->host_stats;
+    if (usum)
+        for (int a = 0; a < 3; ++a) usum[a] = s->checks > 0 ? r[kStatUx + a] : 0.0;
+    if (du2) *du2 = s->checks > 0 ? r[kStatDu2] : 0.0;
+    if (u2) *u2 = s->checks > 0 ? r[kStatU2] : 0.0;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_hash_offset(lbm_solver* s, int64_t offset) {
+    lbm_status v = enter(s);
+    if (v != LBM_OK) return v;
+    // the hash input is the cell index plus the offset modulo 2^32
+    s->kp.hash_offset = (uint32_t)(uint64_t)offset;
+    for (int k = 0; k < 2; ++k)   // captured graphs hold the old kernel parameters
+        if (s->graph[k]) {
+            cudaGraphExecDestroy(s->graph[k]);
+            s->graph[k] = nullptr;
+        }
+    return LBM_OK;
+}
+
+static int face_count(int lat) {
+    switch (lat) {
+    case LBM_D3Q15: return face_count_D3Q15();
+    case LBM_D3Q19: return face_count_D3Q19();
+    case LBM_D3Q27: return face_count_D3Q27();
+    default: return face_count_D2Q9();
+    }
+}
+
+lbm_status lbm_halo_bytes(const lbm_solver* s, size_t* bytes) {
+    if (!s || !bytes) return fail(LBM_EINVAL, "NULL argument");
+    if (!(s->p.flags & LBM_FLAG_Z_GHOSTS)) return fail(LBM_EINVAL, "the solver has no ghost planes");
+    *bytes = (size_t)face_count(s->lat) * s->nx * s->ny * storage_bytes(s->p.storage);
+    return LBM_OK;
+}
+
+static lbm_status halo(lbm_solver* s, int side, void* buf, bool pack) {
+    lbm_status v = enter(s);
+    if (v != LBM_OK) return v;
+    if (!(s->p.flags & LBM_FLAG_Z_GHOSTS)) return fail(LBM_EINVAL, "the solver has no ghost planes");
+    if (side != 0 && side != 1) return fail(LBM_EINVAL, "side must be 0 (lower face) or 1 (upper face)");
+    if (!buf) return fail(LBM_EINVAL, "buffer is NULL");
+    if (((uintptr_t)buf % storage_bytes(s->p.storage)) != 0)
+        return fail(LBM_EINVAL, "buffer must be aligned to the storage element");
+    void* f = s->f[s->cur];
+    cudaError_t e;
+    switch (s->lat) {
+    case LBM_D3Q15: e = launch_halo_D3Q15(s->p.storage, s->kp, f, buf, side, pack, s->stream); break;
+    case LBM_D3Q19: e = launch_halo_D3Q19(s->p.storage, s->kp, f, buf, side, pack, s->stream); break;
+    default: e = launch_halo_D3Q27(s->p.storage, s->kp, f, buf, side, pack, s->stream); break;
+    }
+    CK(s, e, pack ? "halo pack kernel" : "halo unpack kernel");
+    return LBM_OK;
+}
+
+lbm_status lbm_halo_pack(lbm_solver* s, int side, void* buf) { return halo(s, side, buf, true); }
+
+lbm_status lbm_halo_unpack(lbm_solver* s, int side, const void* buf) {
+    return halo(s, side, const_cast<void*>(buf), false);
+}
+
 lbm_status lbm_get_info(const lbm_solver* s, lbm_info* info) {
     if (!s || !info) return fail(LBM_EINVAL, "NULL argument");
     info->lattice = s->lat;
@@ -880,7 +975,7 @@ lbm_status lbm_get_info(const lbm_solver* s, lbm_info* info) {
 // device array instead of the solver's workspace.
 namespace {
 
-constexpr int kStaticParts = 1216;   // = the grid cap of reduce_grid()
+constexpr int kStaticParts = kReduceGridCap;   // reduce_grid() never launches more blocks
 static __device__ __align__(256) double g_static_partials[kStaticParts * kNumStats];
 
 constexpr int kMaxDevices = 64;

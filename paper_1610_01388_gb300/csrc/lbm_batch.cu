@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <atomic>
@@ -27,11 +28,23 @@ using namespace blbm;
 namespace {
 
 constexpr int kMaxSlots = 8192;     // domains resident at once
+constexpr int kFlowChangeSlot = kStatFlowChange;
+static_assert(kFlowChangeSlot == kNumStats - 1 && kStatNonFinite < kFlowChangeSlot,
+              "the flow change takes the stats row's last entry, which check steps leave at 0");
 constexpr int kGraphLen = 16;       // steps per captured graph (even)
 
+// Per domain: the fixed-order sum of its tiles' partials into its stats row,
+// and in the row's last entry the relative change of the flow-rate vector
+// against the row's previous contents, |S - S_prev| / |S| with S the sums of
+// u_real over fluid cells (the change of the mean velocity vector); -1 when
+// the row held no previous check (lbm_batch_add clears it).
 __global__ void k_finalize_domains(const BatchDesc* __restrict__ descs,
                                    const double* __restrict__ partials, double* __restrict__ slots) {
     const BatchDesc& D = descs[blockIdx.x];
+    double* row = slots + (int64_t)D.slot * kNumStats;
+    double prev[3] = {0.0, 0.0, 0.0};
+    if (threadIdx.x == 0)
+        for (int a = 0; a < 3; ++a) prev[a] = row[kStatUx + a];   // read before the row is rewritten
     double v[kNumStats];
 #pragma unroll
     for (int k = 0; k < kNumStats; ++k) v[k] = 0.0;
@@ -49,17 +62,27 @@ __global__ void k_finalize_domains(const BatchDesc* __restrict__ descs,
             for (int k = 0; k < kNumStats; ++k) sm[threadIdx.x][k] += sm[threadIdx.x + o][k];
         __syncthreads();
     }
-    if (threadIdx.x < kNumStats) slots[(int64_t)D.slot * kNumStats + threadIdx.x] = sm[0][threadIdx.x];
+    if (threadIdx.x < kFlowChangeSlot) row[threadIdx.x] = sm[0][threadIdx.x];
+    if (threadIdx.x == 0) {
+        double d2 = 0.0, s2 = 0.0, p2 = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            const double cur = sm[0][kStatUx + a];
+            d2 += (cur - prev[a]) * (cur - prev[a]);
+            s2 += cur * cur;
+            p2 += prev[a] * prev[a];
+        }
+        row[kFlowChangeSlot] = (p2 > 0.0 && s2 > 0.0) ? sqrt(d2 / s2) : -1.0;
+    }
 }
 
 cudaError_t launch_batch(int lat, int model, int storage, bool check, const BatchDesc* d,
                          const int* bd, int nblocks, int grid, int phase, double* partials,
-                         cudaStream_t st) {
+                         int threads, int cpt, cudaStream_t st) {
     switch (lat) {
-    case LBM_D2Q9: return launch_step_batch_D2Q9(model, storage, check, d, bd, nblocks, grid, phase, partials, st);
-    case LBM_D3Q15: return launch_step_batch_D3Q15(model, storage, check, d, bd, nblocks, grid, phase, partials, st);
-    case LBM_D3Q19: return launch_step_batch_D3Q19(model, storage, check, d, bd, nblocks, grid, phase, partials, st);
-    default: return launch_step_batch_D3Q27(model, storage, check, d, bd, nblocks, grid, phase, partials, st);
+    case LBM_D2Q9: return launch_step_batch_D2Q9(model, storage, check, d, bd, nblocks, grid, phase, partials, threads, cpt, st);
+    case LBM_D3Q15: return launch_step_batch_D3Q15(model, storage, check, d, bd, nblocks, grid, phase, partials, threads, cpt, st);
+    case LBM_D3Q19: return launch_step_batch_D3Q19(model, storage, check, d, bd, nblocks, grid, phase, partials, threads, cpt, st);
+    default: return launch_step_batch_D3Q27(model, storage, check, d, bd, nblocks, grid, phase, partials, threads, cpt, st);
     }
 }
 
@@ -67,12 +90,17 @@ struct Group {
     int lat = 0, model = 0, storage = 0;   // model: kernel-side model code
     int user_model = 0;                    // lbm_model, the schedule key
     std::vector<int64_t> ids;
-    int nblocks = 0;                       // tiles of kBlock cells
-    int grid = 0;                          // CTAs per launch (== nblocks: one per tile)
+    int nblocks = 0;                       // check steps: tiles of kBlock cells
+    int grid = 0;                          // check steps: CTAs per launch
+    int tile_threads = kBlock;             // plain steps: tile shape of the schedule
+    int tile_cpt = 1;
+    int pnblocks = 0;                      // plain steps: tiles of tile_threads x tile_cpt cells
+    int pgrid = 0;                         // plain steps: CTAs per launch
     BatchDesc* d_desc = nullptr;
     int* d_block_dom = nullptr;
+    int* d_pblock_dom = nullptr;
     double* d_partials = nullptr;
-    int cap_desc = 0, cap_blocks = 0;
+    int cap_desc = 0, cap_blocks = 0, cap_pblocks = 0;
 };
 
 struct Dom {
@@ -94,6 +122,7 @@ double now_s() {
 // groups as concurrent branches.  Batches adopt a change at their next step.
 std::mutex g_sched_mu;
 std::map<int, int> g_sched_ctas;
+std::map<int, std::map<int, std::pair<int, int>>> g_sched_tile;   // key -> size class -> shape
 std::atomic<int> g_sched_concurrent{0};
 std::atomic<uint64_t> g_sched_version{1};
 
@@ -105,12 +134,43 @@ int sched_ctas(int lat, int model, int storage) {
     return it == g_sched_ctas.end() ? 0 : it->second;
 }
 
+// size class of a group: floor(log2) of its domains' mean cell count
+int batch_size_class(int64_t cells) {
+    int c = 0;
+    while (c < 62 && ((int64_t)1 << (c + 1)) <= cells) ++c;
+    return c;
+}
+
+// Plain-step tile shape for a group of this class: the entry of the class,
+// else the entry of the nearest class set for (lattice, model, storage),
+// else 256 x 1.
+std::pair<int, int> sched_tile(int lat, int model, int storage, int cls) {
+    std::lock_guard<std::mutex> lk(g_sched_mu);
+    auto it = g_sched_tile.find(sched_key(lat, model, storage));
+    if (it == g_sched_tile.end() || it->second.empty()) return {kBlock, 1};
+    int best = -1, dist = 1 << 30;
+    for (const auto& kv : it->second) {
+        const int d = std::abs(kv.first - cls);
+        if (d < dist) {
+            dist = d;
+            best = kv.first;
+        }
+    }
+    return it->second.at(best);
+}
+
+bool valid_tile(int threads, int cpt) {
+    return (threads == 128 || threads == 256 || threads == 512) && (cpt == 1 || cpt == 2) &&
+           !(threads == 512 && cpt == 2);
+}
+
 }  // namespace
 
 void blbm::clear_batch_schedule() {
     {
         std::lock_guard<std::mutex> lk(g_sched_mu);
         g_sched_ctas.clear();
+        g_sched_tile.clear();
     }
     g_sched_concurrent.store(0);
     g_sched_version.fetch_add(1);
@@ -205,9 +265,11 @@ lbm_status rebuild(lbm_batch* b) {
                 if (o.lat == g->lat && o.model == g->model && o.storage == g->storage && o.d_desc) {
                     g->d_desc = o.d_desc;
                     g->d_block_dom = o.d_block_dom;
+                    g->d_pblock_dom = o.d_pblock_dom;
                     g->d_partials = o.d_partials;
                     g->cap_desc = o.cap_desc;
                     g->cap_blocks = o.cap_blocks;
+                    g->cap_pblocks = o.cap_pblocks;
                     o.d_desc = nullptr;
                 }
         }
@@ -217,12 +279,23 @@ lbm_status rebuild(lbm_batch* b) {
         if (o.d_desc) {
             cudaFreeAsync(o.d_desc, b->stream);
             cudaFreeAsync(o.d_block_dom, b->stream);
+            if (o.d_pblock_dom) cudaFreeAsync(o.d_pblock_dom, b->stream);
             cudaFreeAsync(o.d_partials, b->stream);
         }
     for (auto& g : b->groups) {
         std::vector<BatchDesc> desc(g.ids.size());
-        std::vector<int> bd;
-        int blocks = 0;
+        std::vector<int> bd, pbd;
+        int blocks = 0, pblocks = 0;
+        // plain-step tile shape of the group's size class (FP64 and the
+        // Newton-implicit PR step: 256 x 1)
+        int64_t cells = 0;
+        for (int64_t id : g.ids) cells += b->doms[id].s->ncells;
+        const int cls = batch_size_class(cells / (int64_t)g.ids.size());
+        std::pair<int, int> shape = sched_tile(g.lat, g.user_model, g.storage, cls);
+        if (g.storage == LBM_F64 || g.model == kModelPRImplicit) shape = {kBlock, 1};
+        g.tile_threads = shape.first;
+        g.tile_cpt = shape.second;
+        const int tile_cells = g.tile_threads * g.tile_cpt;
         for (size_t j = 0; j < g.ids.size(); ++j) {
             Dom& d = b->doms[g.ids[j]];
             const lbm_solver* s = d.s;
@@ -241,12 +314,18 @@ lbm_status rebuild(lbm_batch* b) {
             D.block_begin = blocks;
             D.nblocks = step_grid(s->ncells);
             D.slot = d.slot;
+            D.pblock_begin = pblocks;
             for (int q = 0; q < D.nblocks; ++q) bd.push_back((int)j);
             blocks += D.nblocks;
+            const int ptiles = (s->ncells + tile_cells - 1) / tile_cells;
+            for (int q = 0; q < ptiles; ++q) pbd.push_back((int)j);
+            pblocks += ptiles;
         }
         g.nblocks = blocks;
+        g.pnblocks = pblocks;
         const int ctas = sched_ctas(g.lat, g.user_model, g.storage);
         g.grid = ctas > 0 ? std::min(blocks, ctas * b->sms) : blocks;
+        g.pgrid = ctas > 0 ? std::min(pblocks, ctas * b->sms) : pblocks;
         if ((int)desc.size() > g.cap_desc) {
             if (g.d_desc) cudaFreeAsync(g.d_desc, b->stream);
             g.cap_desc = (int)desc.size() * 2;
@@ -259,8 +338,14 @@ lbm_status rebuild(lbm_batch* b) {
             BCK(b, cudaMallocAsync((void**)&g.d_block_dom, sizeof(int) * g.cap_blocks, b->stream), "batch block map");
             BCK(b, cudaMallocAsync((void**)&g.d_partials, sizeof(double) * kNumStats * g.cap_blocks, b->stream), "batch partials");
         }
+        if (pblocks > g.cap_pblocks) {
+            if (g.d_pblock_dom) cudaFreeAsync(g.d_pblock_dom, b->stream);
+            g.cap_pblocks = pblocks * 2;
+            BCK(b, cudaMallocAsync((void**)&g.d_pblock_dom, sizeof(int) * g.cap_pblocks, b->stream), "batch tile map");
+        }
         BCK(b, cudaMemcpyAsync(g.d_desc, desc.data(), sizeof(BatchDesc) * desc.size(), cudaMemcpyHostToDevice, b->stream), "batch table upload");
         BCK(b, cudaMemcpyAsync(g.d_block_dom, bd.data(), sizeof(int) * bd.size(), cudaMemcpyHostToDevice, b->stream), "batch block map upload");
+        BCK(b, cudaMemcpyAsync(g.d_pblock_dom, pbd.data(), sizeof(int) * pbd.size(), cudaMemcpyHostToDevice, b->stream), "batch tile map upload");
         // pageable sources: make sure the copies are done before the vectors go
         BCK(b, cudaStreamSynchronize(b->stream), "batch table sync");
     }
@@ -269,8 +354,11 @@ lbm_status rebuild(lbm_batch* b) {
 }
 
 cudaError_t launch_group(lbm_batch* b, const Group& g, bool check, int phase, cudaStream_t st) {
-    cudaError_t e = launch_batch(g.lat, g.model, g.storage, check, g.d_desc, g.d_block_dom,
-                                 g.nblocks, g.grid, phase, g.d_partials, st);
+    cudaError_t e = check ? launch_batch(g.lat, g.model, g.storage, true, g.d_desc, g.d_block_dom,
+                                         g.nblocks, g.grid, phase, g.d_partials, kBlock, 1, st)
+                          : launch_batch(g.lat, g.model, g.storage, false, g.d_desc,
+                                         g.d_pblock_dom, g.pnblocks, g.pgrid, phase, nullptr,
+                                         g.tile_threads, g.tile_cpt, st);
     if (e != cudaSuccess || !check) return e;
     k_finalize_domains<<<(int)g.ids.size(), kBlock, 0, st>>>(g.d_desc, g.d_partials, b->d_slots);
     return cudaGetLastError();
@@ -420,6 +508,15 @@ lbm_status lbm_batch_add(lbm_batch* b, lbm_lattice lat, int nx, int ny, int nz,
     d.bytes = bytes;
     d.parity0 = b->phase ^ s->cur;
     d.slot = b->free_slots.back();
+    // a reused row holds its last occupant's stats: the first check step of
+    // this domain must find it empty
+    if (cudaMemsetAsync(b->d_slots + (int64_t)d.slot * kNumStats, 0, kNumStats * sizeof(double),
+                        b->stream) != cudaSuccess) {
+        lbm_destroy(s);
+        cudaFreeAsync(ws, b->stream);
+        return bfail(b, cudaGetLastError(), "stats row reset");
+    }
+    std::memset(b->h_slots + (int64_t)d.slot * kNumStats, 0, kNumStats * sizeof(double));
     b->free_slots.pop_back();
     *id = b->next_id++;
     b->doms[*id] = d;
@@ -500,6 +597,7 @@ lbm_status lbm_batch_domain_status(lbm_batch* b, int64_t id, lbm_domain_status* 
     for (int a = 0; a < 3; ++a) st->flow[a] = d.checks > 0 ? r[kStatUx + a] / len[a] : 0.0;
     st->residual = (d.checks >= 2 && r[kStatU2] > 0.0) ? std::sqrt(r[kStatDu2] / r[kStatU2]) : -1.0;
     st->nonfinite = (d.checks > 0 && r[kStatNonFinite] != 0.0) ? 1 : 0;
+    st->flow_change = d.checks >= 2 ? r[kStatFlowChange] : -1.0;
     return LBM_OK;
 }
 
@@ -547,6 +645,40 @@ lbm_status lbm_tuning_get_batch(lbm_lattice lat, int32_t model, int32_t storage,
     return LBM_OK;
 }
 
+lbm_status lbm_tuning_set_batch_tile(lbm_lattice lat, int32_t model, int32_t storage,
+                                     int32_t size_class, int32_t threads, int32_t cells_per_thread) {
+    if (lattice_q(lat) == 0) return fail(LBM_EINVAL, "unknown lattice %d", lat);
+    if (model != LBM_MODEL_PR && model != LBM_MODEL_IR) return fail(LBM_EINVAL, "unknown model %d", model);
+    if (storage_bytes(storage) == 0) return fail(LBM_EINVAL, "unknown storage %d", storage);
+    if (size_class < 0 || size_class > 62) return fail(LBM_EINVAL, "size_class must be in 0..62");
+    if (!valid_tile(threads, cells_per_thread))
+        return fail(LBM_EINVAL, "tile shape %d x %d is not one of 128/256/512 x 1, 128/256 x 2",
+                    threads, cells_per_thread);
+    if (storage == LBM_F64 && !(threads == kBlock && cells_per_thread == 1))
+        return fail(LBM_EINVAL, "FP64 storage runs 256 x 1 tiles only");
+    {
+        std::lock_guard<std::mutex> lk(g_sched_mu);
+        g_sched_tile[sched_key(lat, model, storage)][size_class] = {threads, cells_per_thread};
+    }
+    g_sched_version.fetch_add(1);
+    return LBM_OK;
+}
+
+lbm_status lbm_tuning_get_batch_tile(lbm_lattice lat, int32_t model, int32_t storage,
+                                     int64_t mean_cells, int32_t* threads,
+                                     int32_t* cells_per_thread, int32_t* size_class) {
+    if (lattice_q(lat) == 0) return fail(LBM_EINVAL, "unknown lattice %d", lat);
+    if (model != LBM_MODEL_PR && model != LBM_MODEL_IR) return fail(LBM_EINVAL, "unknown model %d", model);
+    if (storage_bytes(storage) == 0) return fail(LBM_EINVAL, "unknown storage %d", storage);
+    if (mean_cells < 1) return fail(LBM_EINVAL, "mean_cells must be >= 1");
+    const int cls = batch_size_class(mean_cells);
+    const std::pair<int, int> t = sched_tile(lat, model, storage, cls);
+    if (threads) *threads = t.first;
+    if (cells_per_thread) *cells_per_thread = t.second;
+    if (size_class) *size_class = cls;
+    return LBM_OK;
+}
+
 lbm_status lbm_tuning_set_batch_concurrency(int32_t concurrent) {
     if (concurrent != 0 && concurrent != 1) return fail(LBM_EINVAL, "concurrent must be 0 or 1");
     g_sched_concurrent.store(concurrent);
@@ -573,6 +705,7 @@ void lbm_batch_destroy(lbm_batch* b) {
     for (auto& g : b->groups) {
         if (g.d_desc) cudaFreeAsync(g.d_desc, b->stream);
         if (g.d_block_dom) cudaFreeAsync(g.d_block_dom, b->stream);
+        if (g.d_pblock_dom) cudaFreeAsync(g.d_pblock_dom, b->stream);
         if (g.d_partials) cudaFreeAsync(g.d_partials, b->stream);
     }
     cudaStreamSynchronize(b->stream);
@@ -599,9 +732,6 @@ struct Req {
     lbm_result res{};
     int64_t dom = 0;
     size_t bytes = 0;
-    int axis = 0;           // largest body-force component: the flow direction
-    double prev_flow = 0.0;
-    bool has_prev = false;
     std::vector<double> fields;   // rho, ux, uy, uz of the final state (keep_fields)
 };
 
@@ -647,6 +777,8 @@ lbm_status lbm_server_submit(lbm_server* s, const lbm_request* req, int64_t* id)
     if (!s || !req || !id) return fail(LBM_EINVAL, "NULL argument");
     if (req->max_steps < 1) return fail(LBM_EINVAL, "max_steps must be >= 1");
     if (!(req->tolerance > 0.0)) return fail(LBM_EINVAL, "tolerance must be > 0");
+    if (req->criterion != LBM_STEADY_FLOW && req->criterion != LBM_STEADY_RESIDUAL)
+        return fail(LBM_EINVAL, "unknown steady-state criterion %d", req->criterion);
     if (req->nx < 1 || req->ny < 1 || req->nz < 1 || !req->solid_mask)
         return fail(LBM_EINVAL, "bad extents or mask");
     lbm_params q = req->params;
@@ -661,8 +793,6 @@ lbm_status lbm_server_submit(lbm_server* s, const lbm_request* req, int64_t* id)
     r.mask.assign(req->solid_mask, req->solid_mask + n);
     r.r.solid_mask = nullptr;
     r.bytes = bytes;
-    for (int a = 1; a < 3; ++a)
-        if (std::fabs(req->params.g[a]) > std::fabs(req->params.g[r.axis])) r.axis = a;
     r.res.state = LBM_REQ_QUEUED;
     r.res.t_submit = now_s() - s->t0;
     *id = s->next_id++;
@@ -743,11 +873,9 @@ lbm_status lbm_server_advance(lbm_server* s, int64_t nsteps, int32_t* completed)
         lbm_domain_status ds;
         if ((v = lbm_batch_domain_status(s->batch, r.dom, &ds)) != LBM_OK) return v;
         int state = -1;
-        const double q = ds.flow[r.axis];
-        const bool steady = r.has_prev && std::fabs(q - r.prev_flow) <= r.r.tolerance * std::fabs(q) &&
-                            q != 0.0;
-        r.prev_flow = q;
-        r.has_prev = ds.checks > 0;
+        // the change between the last two check steps (check_every apart)
+        const double change = r.r.criterion == LBM_STEADY_RESIDUAL ? ds.residual : ds.flow_change;
+        const bool steady = change >= 0.0 && change < r.r.tolerance;
         if (ds.nonfinite) state = LBM_REQ_FAILED;
         else if (steady) state = LBM_REQ_CONVERGED;
         else if (ds.steps >= r.r.max_steps) state = LBM_REQ_CAPPED;

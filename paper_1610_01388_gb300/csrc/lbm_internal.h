@@ -31,12 +31,16 @@ struct KParams {
     double g[3];
     uint32_t flags;
     int newton;           // PR: Newton iterations of the implicit tau update (0 = explicit)
+    uint32_t hash_offset; // added to the cell index in the stochastic-rounding hash
     FastDiv div_nx, div_ny;   // idx -> (x, y, z) without integer division
 };
 
 // Reduction slots.  Check step: flow sums of u_real (x,y,z), sum |u-u_prev|^2,
 // sum |u|^2, sum of density offsets, count of non-finite densities.
 enum { kStatUx = 0, kStatUy, kStatUz, kStatDu2, kStatU2, kStatDrho, kStatNonFinite };
+// Batch stats rows only: relative change of the mean velocity vector since the
+// domain's previous check step (-1 before its second one).
+enum { kStatFlowChange = 7 };
 // Totals mode: mass offset, momentum x,y,z.
 enum { kTotMass = 0, kTotJx, kTotJy, kTotJz };
 
@@ -51,6 +55,7 @@ struct StepArgs {
     int parity;          // which of the two counters this launch reads
     int block;           // threads per block of plain steps (128, 256 or 512)
     int cpt;             // cells per thread of plain steps (1, or 2 with block 128 / 256)
+    int copy;            // 16-bit PR: solid cells of mixed warps copy through (geometry choice)
 };
 
 enum ReduceMode { kReduceFlow = 0, kReduceTotals = 1 };
@@ -74,10 +79,13 @@ struct BatchDesc;   // per-domain descriptor of a batched launch (kernels.cuh)
     void lattice_table_##L(int* c, double* w);                                                  \
     cudaError_t launch_gather_##L(int storage, const KParams& kp, const void* f,               \
                                   const int64_t* cells, int n, double* out, cudaStream_t st);   \
+    cudaError_t launch_halo_##L(int storage, const KParams& kp, void* f, void* buf, int side,   \
+                                bool pack, cudaStream_t st);                                    \
+    int face_count_##L();                                                                       \
     cudaError_t launch_step_batch_##L(int model, int storage, bool check,                       \
                                       const struct BatchDesc* descs, const int* block_dom,      \
                                       int nblocks, int grid, int phase, double* partials,       \
-                                      cudaStream_t st);
+                                      int threads, int cpt, cudaStream_t st);
 
 BLBM_DECLARE_LAUNCHERS(D2Q9)
 BLBM_DECLARE_LAUNCHERS(D3Q15)
@@ -87,10 +95,14 @@ BLBM_DECLARE_LAUNCHERS(D3Q27)
 cudaError_t launch_finalize(const double* partials, int nparts, double* out, cudaStream_t st);
 cudaError_t launch_fill(void* p, int64_t n, int rsize, double value, cudaStream_t st);
 
+// Most blocks a grid-stride reduction (k_reduce) launches: 152 SMs x 8
+// blocks.  Every buffer of per-block reduction partials is sized by it.
+constexpr int kReduceGridCap = 1216;
+
 inline int step_grid(int ncells) { return (ncells + kBlock - 1) / kBlock; }
 inline int reduce_grid(int ncells) {
     int g = (ncells + kBlock - 1) / kBlock;
-    return g < 1216 ? g : 1216;   // 152 SMs x 8 blocks
+    return g < kReduceGridCap ? g : kReduceGridCap;
 }
 
 }  // namespace blbm

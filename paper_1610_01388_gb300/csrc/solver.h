@@ -62,5 +62,6 @@ struct lbm_solver {
     int graph_len = 64;
     int block = 256;                   // threads per block of plain steps (tuning table)
     int cpt = 1;                       // cells per thread of plain steps (tuning table)
+    int copy = 1;                      // copy-through choice of the 16-bit PR step (geometry)
     uint64_t tune_version = ~uint64_t(0);
 };

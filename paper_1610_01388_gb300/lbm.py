@@ -27,6 +27,7 @@ LBM_F64, LBM_F32, LBM_F16_OFS, LBM_BF16_OFS = 0, 1, 2, 3
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ENONFINITE, LBM_ETIMEOUT, LBM_EBUSY, \
     LBM_EUNSUPPORTED = range(8)
 LBM_FLAG_BURNETT_X = 0x1
+LBM_FLAG_Z_GHOSTS = 0x2
 
 LATTICES = {"D2Q9": LBM_D2Q9, "D3Q15": LBM_D3Q15, "D3Q19": LBM_D3Q19, "D3Q27": LBM_D3Q27}
 MODELS = {"PR": LBM_MODEL_PR, "IR": LBM_MODEL_IR}
@@ -43,8 +44,12 @@ EXPORTED = ["lbm_params_default", "lbm_lattice_info", "lbm_workspace_bytes", "lb
             "lbm_tuning_set", "lbm_tuning_get", "lbm_tuning_clear", "lbm_set_wait_limit",
             "lbm_get_wait_limit", "lbm_get_populations_cells", "lbm_tuning_set_shape",
             "lbm_tuning_get_shape", "lbm_tuning_set_batch", "lbm_tuning_get_batch",
-            "lbm_tuning_set_batch_concurrency", "lbm_tuning_get_batch_concurrency"]
+            "lbm_tuning_set_batch_concurrency", "lbm_tuning_get_batch_concurrency",
+            "lbm_tuning_set_batch_tile", "lbm_tuning_get_batch_tile",
+            "lbm_halo_bytes", "lbm_halo_pack", "lbm_halo_unpack", "lbm_set_hash_offset",
+            "lbm_check_sums"]
 LBM_REQ_QUEUED, LBM_REQ_RUNNING, LBM_REQ_CONVERGED, LBM_REQ_CAPPED, LBM_REQ_FAILED = range(5)
+LBM_STEADY_FLOW, LBM_STEADY_RESIDUAL = 0, 1
 
 
 class LbmError(RuntimeError):
@@ -74,14 +79,15 @@ class lbm_info(ctypes.Structure):
 class lbm_domain_status(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int64), ("checks", ctypes.c_int64),
                 ("residual", ctypes.c_double), ("flow", ctypes.c_double * 3),
-                ("nonfinite", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("nonfinite", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("flow_change", ctypes.c_double)]
 
 
 class lbm_request(ctypes.Structure):
     _fields_ = [("lattice", ctypes.c_int32), ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
                 ("nz", ctypes.c_int32), ("solid_mask", ctypes.c_void_p), ("params", lbm_params),
                 ("tolerance", ctypes.c_double), ("max_steps", ctypes.c_int64),
-                ("keep_fields", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("keep_fields", ctypes.c_int32), ("criterion", ctypes.c_int32)]
 
 
 class lbm_result(ctypes.Structure):
@@ -152,6 +158,13 @@ def library():
             "lbm_tuning_get_batch": [i32, i32, i32, P(i32)],
             "lbm_tuning_set_batch_concurrency": [i32],
             "lbm_tuning_get_batch_concurrency": [P(i32)],
+            "lbm_tuning_set_batch_tile": [i32, i32, i32, i32, i32, i32],
+            "lbm_halo_bytes": [vp, P(sz)],
+            "lbm_halo_pack": [vp, i32, vp],
+            "lbm_halo_unpack": [vp, i32, vp],
+            "lbm_set_hash_offset": [vp, i64],
+            "lbm_check_sums": [vp, vp, P(d), P(d)],
+            "lbm_tuning_get_batch_tile": [i32, i32, i32, i64, P(i32), P(i32), P(i32)],
             "lbm_get_wait_limit": [P(d)],
         }
         for name, args in sig.items():
@@ -375,6 +388,21 @@ def lbm_tuning_get_batch(lat, model, storage) -> int:
     return v.value
 
 
+def lbm_tuning_set_batch_tile(lat, model, storage, size_class, threads, cells_per_thread):
+    _check(library().lbm_tuning_set_batch_tile(_lat(lat), _mdl(model), _sto(storage),
+                                               int(size_class), int(threads),
+                                               int(cells_per_thread)))
+
+
+def lbm_tuning_get_batch_tile(lat, model, storage, mean_cells):
+    """(threads, cells per thread, size class) a group of this mean size runs."""
+    t, c, k = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(library().lbm_tuning_get_batch_tile(_lat(lat), _mdl(model), _sto(storage),
+                                               int(mean_cells), ctypes.byref(t), ctypes.byref(c),
+                                               ctypes.byref(k)))
+    return t.value, c.value, k.value
+
+
 def lbm_tuning_set_batch_concurrency(on):
     _check(library().lbm_tuning_set_batch_concurrency(1 if on else 0))
 
@@ -391,6 +419,32 @@ def lbm_get_populations_cells(h, cells, Q):
     out = np.zeros((Q, cells.size), np.float64)
     _check(library().lbm_get_populations_cells(h, _ptr(cells), cells.size, _ptr(out)))
     return out
+
+
+def lbm_halo_bytes(h) -> int:
+    b = ctypes.c_size_t()
+    _check(library().lbm_halo_bytes(h, ctypes.byref(b)))
+    return b.value
+
+
+def lbm_halo_pack(h, side, buf_ptr):
+    _check(library().lbm_halo_pack(h, int(side), ctypes.c_void_p(buf_ptr)))
+
+
+def lbm_halo_unpack(h, side, buf_ptr):
+    _check(library().lbm_halo_unpack(h, int(side), ctypes.c_void_p(buf_ptr)))
+
+
+def lbm_set_hash_offset(h, offset):
+    _check(library().lbm_set_hash_offset(h, int(offset)))
+
+
+def lbm_check_sums(h):
+    """(usum[3], du2, u2) of the last check step."""
+    us = (ctypes.c_double * 3)()
+    du2, u2 = ctypes.c_double(), ctypes.c_double()
+    _check(library().lbm_check_sums(h, us, ctypes.byref(du2), ctypes.byref(u2)))
+    return np.array(list(us)), du2.value, u2.value
 
 
 def lbm_set_wait_limit(seconds):
@@ -567,7 +621,9 @@ class Server:
                                            int(check_every), ctypes.c_void_p(stream or 0)))
 
     def submit(self, lattice, mask, tolerance=1e-6, max_steps=100000, keep_fields=False,
-               **params):
+               criterion="flow", **params):
+        """criterion "flow": relative change of the mean velocity vector per
+        check interval below tolerance; "residual": the field residual."""
         mask = np.ascontiguousarray(mask, np.uint8)
         if mask.ndim == 2:
             mask = mask[None]
@@ -579,6 +635,7 @@ class Server:
         r.tolerance = float(tolerance)
         r.max_steps = int(max_steps)
         r.keep_fields = 1 if keep_fields else 0
+        r.criterion = {"flow": LBM_STEADY_FLOW, "residual": LBM_STEADY_RESIDUAL}[criterion]
         i = ctypes.c_int64()
         _check(library().lbm_server_submit(self.h, ctypes.byref(r), ctypes.byref(i)))
         return i.value

@@ -263,8 +263,10 @@ def _pooled_porous(side: int, seed: int, r_min: float, r_max: float):
 def serving_requests(n: int = 200, rate: float = 40.0, seed: int = 7, storage: str = "F16",
                      channel_widths=(16, 256), duct_sides=(32, 96), duct_length: int = 64,
                      porous_sides=(32, 64), max_steps: int = 2000, tolerance: float = 1e-4,
-                     porous_radius=(4.0, 6.0), porous_pool: int = 0):
-    """Poisson stream of independent solves: 2D channels (D2Q9, 4 x width),
+                     porous_radius=(4.0, 6.0), porous_pool: int = 0, criterion: str = "flow",
+                     channel_length: int = 4):
+    """Poisson stream of independent solves: 2D channels (D2Q9, channel_length
+    x width, periodic along the length),
     square ducts (D3Q19/D3Q27, side x side x length) and porous boxes
     (D3Q19/D3Q27, random spheres of radius U[porous_radius], porosity 0.7),
     Bingham number uniform in [0.1, 10], model PR or IR with equal
@@ -286,7 +288,7 @@ def serving_requests(n: int = 200, rate: float = 40.0, seed: int = 7, storage: s
         model = "PR" if rng.integers(2) == 0 else "IR"
         if kind == 0:
             w = int(rng.integers(channel_widths[0], channel_widths[1] + 1))
-            mask = channel_mask(4, w + 1)
+            mask = channel_mask(channel_length, w + 1)
             p = channel_params(H=w, nu_p=0.1, u_newton=0.02, bn=bn)
             lat, g = "D2Q9", (p["g"], 0.0, 0.0)
         elif kind == 1:
@@ -307,5 +309,6 @@ def serving_requests(n: int = 200, rate: float = 40.0, seed: int = 7, storage: s
         out.append({"arrival": t, "lattice": lat, "mask": mask, "model": model,
                     "storage": storage, "mu_p": 0.1, "sigma_y": p["sigma_y"], "m": 1e6,
                     "g": g, "tolerance": tolerance, "max_steps": max_steps,
-                    "kind": ("channel", "duct", "porous")[kind], "bn": bn})
+                    "criterion": criterion, "kind": ("channel", "duct", "porous")[kind],
+                    "bn": bn})
     return out

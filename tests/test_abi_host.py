@@ -97,11 +97,26 @@ def _create_status(lat, mask, **kw):
     ("D3Q19", np.zeros((2, 2, 2)), {"model": "PR", "newton_iters": -1}, "newton_iters"),
     ("D3Q19", np.zeros((2, 2, 2)), {"model": "PR", "newton_iters": 65}, "newton_iters"),
     ("D3Q19", np.zeros((2, 2, 2)), {"reserved": 1}, "reserved"),
+    ("D3Q19", np.zeros((2, 2, 2)), {"flags": 0x2}, "ghost planes"),            # nz < 3
+    ("D2Q9", np.zeros((1, 4, 4)), {"flags": 0x2}, "ghost planes"),
+    # ghost planes are not stepped: a slab whose interior is all solid has no fluid
+    ("D3Q19", np.concatenate([np.zeros((1, 2, 2)), np.ones((1, 2, 2)), np.zeros((1, 2, 2))]),
+     {"flags": 0x2}, "no fluid"),
 ])
 def test_create_rejects_invalid_arguments(lat, mask, kw, expect):
     st, msg = _create_status(lat, mask, **kw)
     assert st == lbm.LBM_EINVAL
     assert expect in msg
+
+
+def test_halo_calls_reject_null_handle():
+    lib = lbm.library()
+    b = ctypes.c_size_t()
+    assert lib.lbm_halo_bytes(None, ctypes.byref(b)) == lbm.LBM_EINVAL
+    assert lib.lbm_halo_pack(None, 0, None) == lbm.LBM_EINVAL
+    assert lib.lbm_halo_unpack(None, 1, None) == lbm.LBM_EINVAL
+    assert lib.lbm_set_hash_offset(None, 5) == lbm.LBM_EINVAL
+    assert lib.lbm_check_sums(None, None, None, None) == lbm.LBM_EINVAL
 
 
 def test_create_rejects_empty_and_oversized_extents():
@@ -180,6 +195,30 @@ def test_batch_schedule_host_logic():
     lbm.lbm_tuning_clear()
     assert lbm.lbm_tuning_get_batch("D3Q27", "PR", "F16") == 0
     assert lbm.lbm_tuning_get_batch_concurrency() is False
+
+
+def test_batch_tile_table_host_logic():
+    """Plain-step tile shape per (lattice, model, storage, size class), with
+    the nearest class of the same group standing in for a missing one."""
+    lbm.lbm_tuning_clear()
+    assert lbm.lbm_tuning_get_batch_tile("D3Q19", "PR", "F16", 100_000) == (256, 1, 16)
+    lbm.lbm_tuning_set_batch_tile("D3Q19", "PR", "F16", 16, 128, 2)
+    lbm.lbm_tuning_set_batch_tile("D3Q19", "PR", "F16", 20, 512, 1)
+    assert lbm.lbm_tuning_get_batch_tile("D3Q19", "PR", "F16", 70_000) == (128, 2, 16)
+    assert lbm.lbm_tuning_get_batch_tile("D3Q19", "PR", "F16", 3_000) == (128, 2, 11)   # nearest: 16
+    assert lbm.lbm_tuning_get_batch_tile("D3Q19", "PR", "F16", 2_000_000) == (512, 1, 20)
+    assert lbm.lbm_tuning_get_batch_tile("D3Q19", "IR", "F16", 70_000) == (256, 1, 16)  # other key
+    assert lbm.lbm_tuning_get_batch_tile("D3Q27", "PR", "F16", 70_000) == (256, 1, 16)
+    lib = lbm.library()
+    assert lib.lbm_tuning_set_batch_tile(2, 0, 2, 16, 512, 2) == lbm.LBM_EINVAL   # 512 x 2
+    assert lib.lbm_tuning_set_batch_tile(2, 0, 2, 16, 64, 1) == lbm.LBM_EINVAL
+    assert lib.lbm_tuning_set_batch_tile(2, 0, 2, 16, 256, 3) == lbm.LBM_EINVAL
+    assert lib.lbm_tuning_set_batch_tile(2, 0, 0, 16, 128, 1) == lbm.LBM_EINVAL   # F64: 256 x 1 only
+    assert lib.lbm_tuning_set_batch_tile(2, 0, 0, 16, 256, 1) == lbm.LBM_OK
+    assert lib.lbm_tuning_set_batch_tile(2, 0, 2, 63, 256, 1) == lbm.LBM_EINVAL
+    assert lib.lbm_tuning_set_batch_tile(9, 0, 2, 16, 256, 1) == lbm.LBM_EINVAL
+    lbm.lbm_tuning_clear()
+    assert lbm.lbm_tuning_get_batch_tile("D3Q19", "PR", "F16", 70_000) == (256, 1, 16)
 
 
 def test_wait_limit_host_logic():

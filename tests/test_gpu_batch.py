@@ -84,17 +84,24 @@ def _run_mix(n, k=50):
     return out
 
 
-@pytest.mark.parametrize("ctas,concurrent", [(1, False), (3, False), (0, True), (2, True)])
-def test_batch_schedule_does_not_change_results(ctas, concurrent):
-    """A persistent grid (ctas_per_sm > 0) and concurrent group branches in
-    the graphs change only the launch shape: populations, residuals and flow
-    rates stay bit for bit those of the default schedule."""
+@pytest.mark.parametrize("ctas,concurrent,tile", [
+    (1, False, (256, 1)), (3, False, (256, 1)), (0, True, (256, 1)), (2, True, (256, 1)),
+    (0, False, (128, 1)), (0, False, (512, 1)), (0, False, (128, 2)), (2, True, (256, 2)),
+])
+def test_batch_schedule_does_not_change_results(ctas, concurrent, tile):
+    """A persistent grid (ctas_per_sm > 0), concurrent group branches in the
+    graphs and the plain-step tile shape change only the launch shape:
+    populations, residuals and flow rates stay bit for bit those of the
+    default schedule."""
     n = 333
     lbm.lbm_tuning_clear()
     ref = _run_mix(n)
     try:
-        for lat, _, prm in _cases():
+        for lat, mask, prm in _cases():
             lbm.lbm_tuning_set_batch(lat, prm["model"], prm["storage"], ctas)
+            if prm["storage"] != "F64":
+                for cls in range(0, 40):
+                    lbm.lbm_tuning_set_batch_tile(lat, prm["model"], prm["storage"], cls, *tile)
         lbm.lbm_tuning_set_batch_concurrency(concurrent)
         got = _run_mix(n)
     finally:
@@ -187,3 +194,148 @@ def test_server_results_same_alone_and_in_mix():
                 assert np.array_equal(other[3], alone[3])
                 assert other[2] == alone[2]
         assert alone[0] in (lbm.LBM_REQ_CONVERGED, lbm.LBM_REQ_CAPPED)
+
+
+# --- the batch and the server against the FP64 oracle ------------------------------
+
+# relative L2 velocity error against the oracle at equal step count
+ORACLE_BAR = {"F64": 1e-10, "F32": 1e-5, "F16": 1e-3}
+
+
+def _oracle_for(lat, mask, prm):
+    import oracle
+    p = oracle.params(model=prm["model"], nu_p=prm["mu_p"], sigma_y=prm.get("sigma_y", 0.0),
+                      m=prm.get("m", 0.0), g=prm["g"], newton=prm.get("newton_iters", 0))
+    return oracle.State(lat, p, mask if mask.ndim == 3 else mask[None])
+
+
+def _rel_l2(u_gpu, u_orc, mask):
+    fl = (mask if mask.ndim == 3 else mask[None]) == 0
+    a, b = u_gpu[:, fl], u_orc[:, fl]
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _oracle_cases():
+    por, _ = W.porous_mask(32, porosity=0.7, r_min=3, r_max=5, seed=4)
+    du = W.duct_params(H=23, nu_p=0.1, u_newton=0.02, bn=2.0)
+    return _cases() + [
+        ("D3Q27", W.duct_mask(12, 24, 24), dict(model="PR", storage="F16", mu_p=0.1,
+                                                sigma_y=du["sigma_y"], m=1e6, g=(du["g"], 0, 0))),
+        ("D3Q19", por, dict(model="IR", storage="F16", mu_p=0.1, sigma_y=1e-6, g=(2e-5, 0, 0))),
+        ("D3Q19", por, dict(model="PR", storage="F32", mu_p=0.1, sigma_y=1e-6, m=1e6,
+                            g=(2e-5, 0, 0))),
+    ]
+
+
+@pytest.mark.parametrize("tile", [(256, 1), (128, 2)])
+def test_batched_domains_match_oracle(tile):
+    """Every domain of a mixed batch (four lattices, both models, FP64, FP32
+    and FP16 storage, the Newton-implicit PR step) after 1000 batched steps
+    against the oracle stepped 1000 times: relative L2 of u_real within 1e-10
+    (FP64), 1e-5 (FP32), 1e-3 (FP16); the last check step's flow rate too
+    (a check step measures the populations it streams: the state after 999
+    steps)."""
+    n, k = 1000, 50
+    lbm.lbm_tuning_clear()
+    try:
+        for lat, _, prm in _oracle_cases():
+            if prm["storage"] != "F64":
+                for cls in range(0, 40):
+                    lbm.lbm_tuning_set_batch_tile(lat, prm["model"], prm["storage"], cls, *tile)
+        b = lbm.Batch(4 * GB, check_every=k)
+        ids = [b.add(lat, mask, **prm) for lat, mask, prm in _oracle_cases()]
+        b.step(n)
+        for (lat, mask, prm), dom in zip(_oracle_cases(), ids):
+            o = _oracle_for(lat, mask, prm)
+            o.step(n - 1)
+            q_check = o.flowrate(0)
+            o.step(1)
+            _, uo = o.fields()
+            _, ug = lbm.lbm_fields(b.solver(dom))
+            err = _rel_l2(ug.reshape(uo.shape), uo, mask)
+            assert err <= ORACLE_BAR[prm["storage"]], (lat, prm, err)
+            st = b.status(dom)
+            assert abs(st.flow[0] - q_check) <= 10 * ORACLE_BAR[prm["storage"]] * abs(q_check), (lat, prm)
+        b.close()
+    finally:
+        lbm.lbm_tuning_clear()
+
+
+def test_served_results_match_oracle():
+    """Requests served in a mix, under a budget that admits about two at a
+    time (queueing and mid-flight admission), each run to its 1000-step cap:
+    the final u_real of every request against the oracle stepped 1000 times,
+    within the same bars as the batch."""
+    reqs = []
+    for lat, mask, prm in _oracle_cases():
+        if prm.get("newton_iters"):
+            continue
+        reqs.append((lat, mask, dict(tolerance=1e-30, max_steps=1000, **prm)))
+    need = []
+    for lat, mask, kw in reqs:
+        prm = {k: v for k, v in kw.items() if k not in ("tolerance", "max_steps")}
+        m3 = mask if mask.ndim == 3 else mask[None]
+        need.append(lbm.lbm_workspace_bytes(lat, m3.shape[2], m3.shape[1], m3.shape[0],
+                                            lbm.lbm_params_default(check_every=100, **prm)))
+    served = _serve(reqs, budget=2 * max(need))
+    for (lat, mask, kw), (state, steps, _, u) in zip(reqs, served):
+        assert state == lbm.LBM_REQ_CAPPED and steps == 1000
+        prm = {k: v for k, v in kw.items() if k not in ("tolerance", "max_steps")}
+        o = _oracle_for(lat, mask, prm)
+        o.step(1000)
+        _, uo = o.fields()
+        err = _rel_l2(u.reshape(uo.shape), uo, mask)
+        assert err <= ORACLE_BAR[prm["storage"]], (lat, prm, err)
+
+
+def test_flow_change_is_the_relative_change_of_the_mean_velocity():
+    """lbm_domain_status.flow_change against the same quantity formed on the
+    host from a single-domain solver's flow rates at two check steps k apart:
+    |S - S_prev| / |S| with S_a = L_a Q_a, the sums of u_real."""
+    lat, mask, prm = _cases()[3]
+    k = 50
+    b = lbm.Batch(GB, check_every=k)
+    dom = b.add(lat, mask, **prm)
+    b.step(k)
+    assert b.status(dom).flow_change == -1.0        # one check step so far
+    ref = lbm.Solver(lat, mask, check_every=k, **prm)
+    L = np.array([mask.shape[2], mask.shape[1], mask.shape[0]], float)
+    ref.step(k - 1)
+    s0 = np.array([ref.flowrate(a) for a in range(3)]) * L
+    b.step(k)
+    ref.step(k)
+    s1 = np.array([ref.flowrate(a) for a in range(3)]) * L
+    want = np.linalg.norm(s1 - s0) / np.linalg.norm(s1)
+    got = b.status(dom).flow_change
+    assert want > 0 and abs(got - want) <= 1e-6 * want, (got, want)
+    ref.close()
+    b.close()
+
+
+def test_server_steady_criteria():
+    """A channel served to steady state under each criterion: the request is
+    retired as converged at the first advance whose last check step shows a
+    change below the tolerance, and not before."""
+    ch = W.channel_params(H=15, nu_p=0.1, u_newton=0.02, bn=0.5)
+    mask = W.channel_mask(4, 16)
+    kw = dict(model="IR", storage="F32", mu_p=0.1, sigma_y=ch["sigma_y"], g=(ch["g"], 0, 0))
+    for crit, tol in (("flow", 1e-7), ("residual", 1e-6)):
+        srv = lbm.Server(GB, check_every=100)
+        rid = srv.submit("D2Q9", mask, tolerance=tol, max_steps=200_000, criterion=crit, **kw)
+        for _ in range(2000):
+            srv.advance(200)
+            if srv.pending()[:2] == (0, 0):
+                break
+        res = srv.result(rid)
+        srv.close()
+        assert res.state == lbm.LBM_REQ_CONVERGED, crit
+        # replay alone: the change at the retiring advance is below tol, the one before is not
+        b = lbm.Batch(GB, check_every=100)
+        dom = b.add("D2Q9", mask, **kw)
+        changes = []
+        while b.status(dom).steps < res.steps:
+            b.step(200)
+            st = b.status(dom)
+            changes.append(st.flow_change if crit == "flow" else st.residual)
+        b.close()
+        assert 0.0 <= changes[-1] < tol and not (0.0 <= changes[-2] < tol), (crit, changes[-3:])

@@ -94,6 +94,53 @@ def test_fullsize_porous_d3q19(model):
                          g=(2e-6, 0.0, 0.0))
 
 
+@pytest.mark.parametrize("model,block", [("PR", 128), ("IR", 256)])
+def test_fullsize_duct_whole_field_equal_steps(model, block):
+    """The bench duct itself (D3Q27, 256 x 128 x 128, 127 x 127 fluid, FP32,
+    Bn = 2, m = 1e6, check step every 100, the block size the bench's tuner
+    picks for the model, CUDA-graph replay), 200 steps from rest on the GPU
+    and in the FP64 oracle: relative L2 of u_real over the whole field within
+    1e-5, and the flow rate within 1e-5."""
+    from _pairs import rel_l2_u
+    prm = W.duct_params(H=127, nu_p=0.1, u_newton=0.02, bn=2.0)
+    mask = W.duct_mask(256, 128, 128)
+    lbm.lbm_tuning_clear()
+    try:
+        _, _, cls = lbm.lbm_tuning_get_shape("D3Q27", model, "F32", mask.size)
+        lbm.lbm_tuning_set_shape("D3Q27", model, "F32", cls, block, 1)
+        s, o = make_pair("D3Q27", mask, model=model, storage="F32", check_every=100, nu_p=0.1,
+                         sigma_y=prm["sigma_y"], m=1e6, g=(prm["g"], 0.0, 0.0))
+        s.step(200)
+        o.step(200)
+        err = rel_l2_u(s, o)
+        print(f"duct 256x128x128 D3Q27 {model} F32, 200 steps: rel L2 u {err:.3e}")
+        assert err <= 1e-5
+        qo = o.flowrate(0)
+        assert abs(s.flowrate(0) - qo) <= 1e-5 * abs(qo)
+        s.close()
+    finally:
+        lbm.lbm_tuning_clear()
+
+
+@pytest.mark.parametrize("model", ["PR", "IR"])
+def test_fullsize_fp16_duct_whole_field_equal_steps(model):
+    """FP16 offset storage on the precision workload's duct cross-section
+    (D3Q27, 191 x 191 fluid, periodic along x, here 16 cells long so the FP64
+    oracle runs it in about a minute), Bn = 2, 1500 steps from rest on both
+    sides: relative L2 of u_real over the whole field within 1e-3."""
+    from _pairs import rel_l2_u
+    prm = W.duct_params(H=191, nu_p=0.1, u_newton=0.02, bn=2.0)
+    mask = W.duct_mask(16, 192, 192)
+    s, o = make_pair("D3Q27", mask, model=model, storage="F16", check_every=100, nu_p=0.1,
+                     sigma_y=prm["sigma_y"], m=1e6, g=(prm["g"], 0.0, 0.0))
+    s.step(1500)
+    o.step(1500)
+    err = rel_l2_u(s, o)
+    print(f"duct 16x192x192 D3Q27 {model} F16, 1500 steps: rel L2 u {err:.3e}")
+    assert err <= 1e-3
+    s.close()
+
+
 def test_fullsize_channel_fp64_20k_steps():
     """Channel 4 x 64, D2Q9, FP64, 20k steps from rest, both models: the whole
     field against the oracle at equal step count."""

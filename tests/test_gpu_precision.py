@@ -1,12 +1,14 @@
 """Reduced-precision storage (FP16 / BF16 offsets, FP32 arithmetic,
 stochastic rounding on store) against the FP64 oracle.
 
-Bar: relative L2 velocity error <= 1e-3 at equal step count on the
-precision-form geometries (square duct and porous box, D3Q27) at sizes the
-oracle runs in seconds -- met by FP16.  BF16 keeps 8 significant bits
-(8x coarser than FP16) and lands at 1.4-1.7e-3 on these flows: it does NOT
-meet the 1e-3 bar, and its tests pin that measured level (<= 2.5e-3) so a
-regression still fails.  Single collisions agree with the oracle up to the
+The reduced-precision form is FP16: relative L2 velocity error <= 1e-3 at
+equal step count on the precision-form geometries (square duct and porous
+box, D3Q27) at sizes the oracle runs in seconds (test_*_velocity_error).
+BF16 keeps 8 significant bits (8x coarser than FP16) and lands at
+1.4-1.7e-3 on these flows: it does NOT meet the 1e-3 bar and is offered only
+as a storage option that fails it.  Its own tests (test_bf16_*_error_level)
+hold it at its measured level, <= 2.5e-3, so that a regression still fails;
+they are not the bar.  Single collisions agree with the oracle up to the
 storage quantum of the outputs.
 """
 import numpy as np
@@ -73,37 +75,49 @@ def _porous_case(storage, model, steps=600):
     return err
 
 
-BAR = {"F16": 1e-3, "BF16": 2.5e-3}
+BAR = 1e-3                 # the reduced-precision bar (FP16)
+BF16_LEVEL = 2.5e-3        # BF16's measured level, held against regressions; fails BAR
 
 
-@pytest.mark.parametrize("storage", ["F16", "BF16"])
-@pytest.mark.parametrize("model", ["PR", "IR"])
-def test_duct_velocity_error(storage, model):
-    err = _duct_case(storage, model)
-    print(f"duct D3Q27 {model} {storage}: rel L2 u error {err:.3e}")
-    assert err <= BAR[storage]
-
-
-@pytest.mark.parametrize("storage", ["F16", "BF16"])
-@pytest.mark.parametrize("model", ["PR", "IR"])
-def test_porous_velocity_error(storage, model):
-    err = _porous_case(storage, model)
-    print(f"porous D3Q27 {model} {storage}: rel L2 u error {err:.3e}")
-    assert err <= BAR[storage]
-
-
-@pytest.mark.parametrize("storage", ["F16", "BF16"])
-@pytest.mark.parametrize("model", ["PR", "IR"])
-def test_duct_velocity_error_two_cells_per_thread(storage, model):
-    """The same bar with plain steps at two cells per thread (packed FP32
-    collision of both cells)."""
+def _two_cells(storage, model):
     mask_cells = 16 * 25 * 25
     lbm.lbm_tuning_clear()
     try:
         _, _, cls = lbm.lbm_tuning_get_shape("D3Q27", model, storage, mask_cells)
         lbm.lbm_tuning_set_shape("D3Q27", model, storage, cls, 128, 2)
-        err = _duct_case(storage, model)
+        return _duct_case(storage, model)
     finally:
         lbm.lbm_tuning_clear()
-    print(f"duct D3Q27 {model} {storage} 2 cells/thread: rel L2 u error {err:.3e}")
-    assert err <= BAR[storage]
+
+
+@pytest.mark.parametrize("model", ["PR", "IR"])
+def test_duct_velocity_error(model):
+    err = _duct_case("F16", model)
+    print(f"duct D3Q27 {model} F16: rel L2 u error {err:.3e}")
+    assert err <= BAR
+
+
+@pytest.mark.parametrize("model", ["PR", "IR"])
+def test_porous_velocity_error(model):
+    err = _porous_case("F16", model)
+    print(f"porous D3Q27 {model} F16: rel L2 u error {err:.3e}")
+    assert err <= BAR
+
+
+@pytest.mark.parametrize("model", ["PR", "IR"])
+def test_duct_velocity_error_two_cells_per_thread(model):
+    """The same bar with plain steps at two cells per thread (packed FP32
+    collision of both cells)."""
+    err = _two_cells("F16", model)
+    print(f"duct D3Q27 {model} F16 2 cells/thread: rel L2 u error {err:.3e}")
+    assert err <= BAR
+
+
+@pytest.mark.parametrize("case", ["duct", "porous", "duct_two_cells"])
+@pytest.mark.parametrize("model", ["PR", "IR"])
+def test_bf16_velocity_error_level(case, model):
+    """BF16 does not meet the 1e-3 bar; this holds it at its measured level."""
+    err = {"duct": lambda: _duct_case("BF16", model), "porous": lambda: _porous_case("BF16", model),
+           "duct_two_cells": lambda: _two_cells("BF16", model)}[case]()
+    print(f"{case} D3Q27 {model} BF16: rel L2 u error {err:.3e} (bar 1e-3 not met)")
+    assert err <= BF16_LEVEL
