@@ -39,11 +39,17 @@ def _duct_for(lattice, cells):
     return W.duct_mask(max(4, cells // (side * side)), side, side)
 
 
-def measure(lattice, model, storage, size_class, steps=300, warmup=70):
-    """Average step time (s) of every candidate launch shape."""
+def measure(lattice, model, storage, size_class, steps=300, warmup=70, mask=None):
+    """Average step time (s) of every candidate launch shape, on `mask` when
+    given (the workload's own geometry), else on a duct of the size class.
+    The geometry matters beyond its size: it decides, among others, whether
+    the 16-bit PR step runs its copy-through form (mixed warps), so a duct
+    whose rows do not fill whole warps can rank the shapes differently from
+    one whose rows do."""
     import torch
     cells = 1 << size_class
-    mask = _duct_for(lattice, cells)
+    if mask is None:
+        mask = _duct_for(lattice, cells)
     out = {}
     for block, cpt in CANDIDATES:
         if cpt == 2 and storage == "F64":
@@ -63,11 +69,12 @@ def measure(lattice, model, storage, size_class, steps=300, warmup=70):
     return out
 
 
-def tune(lattice, model, storage, cells, cache=None, steps=300):
-    """Tune the size class of `cells`; returns (best (block, cells per thread),
-    {(block, cells per thread): seconds})."""
+def tune(lattice, model, storage, cells, cache=None, steps=300, mask=None):
+    """Tune the size class of `cells` (on `mask`, the workload's geometry,
+    when given); returns (best (block, cells per thread), {(block, cells per
+    thread): seconds})."""
     _, cls = lbm.lbm_tuning_get(lattice, model, storage, cells)
-    times = measure(lattice, model, storage, cls, steps=steps)
+    times = measure(lattice, model, storage, cls, steps=steps, mask=mask)
     best = min(times, key=times.get)
     lbm.lbm_tuning_set_shape(lattice, model, storage, cls, *best)
     if cache:

@@ -156,11 +156,14 @@ class RankRing:
         above, below = (self.rank + 1) % self.world, (self.rank - 1) % self.world
         peer = (lambda r: d.get_global_rank(self.group, r)) if self.group is not None else (lambda r: r)
         self._sync_device()
-        reqs = [d.isend(up, peer(above), group=self.group, tag=0),
-                d.irecv(self._recv[0], peer(below), group=self.group, tag=0),
-                d.isend(down, peer(below), group=self.group, tag=1),
-                d.irecv(self._recv[1], peer(above), group=self.group, tag=1)]
-        for r in reqs:
+        # one group of point-to-point operations: NCCL runs separately issued
+        # sends and receives in order on its stream, so two ranks that both
+        # send first would wait on each other
+        ops = [d.P2POp(d.isend, up, peer(above), self.group, 0),
+               d.P2POp(d.irecv, self._recv[0], peer(below), self.group, 0),
+               d.P2POp(d.isend, down, peer(below), self.group, 1),
+               d.P2POp(d.irecv, self._recv[1], peer(above), self.group, 1)]
+        for r in d.batch_isend_irecv(ops):
             r.wait()
         self.slab.unpack(0, self._recv[0])
         self.slab.unpack(1, self._recv[1])
