@@ -20,9 +20,10 @@ larger than L2, so no flush is needed between steps.
 
 Also reported, outside the timed region: the porous box of the porous-medium
 workload (256^3, D3Q19, FP32 and FP16 storage, both models) with its own
-roofline, the same metric end to end through the C ABI with host buffers,
-and the continuous-batching server on a Poisson stream of independent solves
-run to steady state.
+roofline, the precision workload's 512x192x192 duct (FP32 and FP16), the
+same metric end to end through the C ABI with host buffers, and the
+continuous-batching server on a Poisson stream of independent solves run to
+steady state.
 
 --impl reference times the FP64 CPU oracle (the correctness reference) on
 the host cores, on a bounded sample of the same duct, one sample per step.
@@ -111,15 +112,15 @@ def workload_mask(nx=None):
 # for the device-code sources they were captured with (KERNEL_FINGERPRINT)
 # and are reported as null once any of those sources changes.
 NCU_TRAFFIC_POROUS = {
-    ("F16", "IR"): 1306306498, ("F16", "PR"): 1435071919, ("F32", "IR"): 2569463680, ("F32", "PR"): 2696823844,
+    ("F16", "IR"): 1306262982, ("F16", "PR"): 1435169166, ("F32", "IR"): 2569450785, ("F32", "PR"): 2696842270,
 }
 NCU_TRAFFIC = {
-    ("F32", "IR", 128, 1): 855791755, ("F32", "IR", 128, 2): 855389199, ("F32", "IR", 256, 1): 855596442, ("F32", "IR", 256, 2): 857069297, ("F32", "IR", 512, 1): 857371644,
-    ("F32", "PR", 128, 1): 890772319, ("F32", "PR", 128, 2): 889922707, ("F32", "PR", 256, 1): 889686506, ("F32", "PR", 256, 2): 890796440, ("F32", "PR", 512, 1): 890194549,
-    ("F16", "IR", 128, 1): 419970321, ("F16", "IR", 128, 2): 419275014, ("F16", "IR", 256, 1): 419751215, ("F16", "IR", 256, 2): 420376707, ("F16", "IR", 512, 1): 420546773,
-    ("F16", "PR", 128, 1): 451338183, ("F16", "PR", 128, 2): 450981847, ("F16", "PR", 256, 1): 451391103, ("F16", "PR", 256, 2): 451153206, ("F16", "PR", 512, 1): 451256527,
+    ("F32", "IR", 128, 1): 855828959, ("F32", "IR", 128, 2): 855420895, ("F32", "IR", 256, 1): 855586898, ("F32", "IR", 256, 2): 857031687, ("F32", "IR", 512, 1): 857374821,
+    ("F32", "PR", 128, 1): 889919270, ("F32", "PR", 128, 2): 889816892, ("F32", "PR", 256, 1): 889681265, ("F32", "PR", 256, 2): 890840825, ("F32", "PR", 512, 1): 890229380,
+    ("F16", "IR", 128, 1): 419953085, ("F16", "IR", 128, 2): 419266469, ("F16", "IR", 256, 1): 419741658, ("F16", "IR", 256, 2): 420161778, ("F16", "IR", 512, 1): 420531845,
+    ("F16", "PR", 128, 1): 451661161, ("F16", "PR", 128, 2): 450987730, ("F16", "PR", 256, 1): 451111067, ("F16", "PR", 256, 2): 451170799, ("F16", "PR", 512, 1): 451244961,
 }
-KERNEL_FINGERPRINT = "fd795ddd93f90f43"
+KERNEL_FINGERPRINT = "a24c4b9b1664c0d1"
 KERNEL_SOURCES = ("kernels.cuh", "lattice.cuh", "lbm_internal.h", "fastdiv.h", "kern_d3q27.cu",
                   "kern_d3q19.cu")
 
@@ -361,6 +362,8 @@ def run_ours(args):
     e2e = run_e2e(args, mask, nfluid, g, sy, dev)
     steady = run_steady(args, mask, nfluid, g, sy) if args.steady else None
     porous = run_porous_record(args) if (args.porous_record > 0 and not POROUS) else None
+    precision = (run_precision_record(args)
+                 if (args.precision_steps > 0 and not POROUS and LATTICE == "D3Q27") else None)
     serving = None
     if args.serve_requests > 0:
         serving = {"form": "served FP16-offset storage (stochastic rounding) vs FP32, batched; "
@@ -385,6 +388,7 @@ def run_ours(args):
                 "config": workload_config({"per_rank": "independent duct pair per GPU",
                                            "fluid_cells": nfluid, "autotuned": tuned}),
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "porous": porous,
+                "precision": precision,
                 "serving": serving, "time_to_steady": steady,
                 "ms_per_step_median": round(statistics.median(step_ms), 5),
                 "ms_per_step_spread": [round(min(step_ms), 5), round(max(step_ms), 5)],
@@ -430,8 +434,9 @@ def run_e2e(args, mask, nfluid, g, sy, dev):
     import torch
     from paper_1610_01388_gb300 import lbm
     K = (args.e2e_steps if args.e2e_steps > 0 else args.steps) * CHECK_EVERY   # lattice steps
-    rho = np.empty(mask.size)
-    u = np.empty((3, mask.size))
+    # pinned host buffers for the read-back
+    rho = torch.empty(mask.size, dtype=torch.float64, pin_memory=True).numpy()
+    u = torch.empty((3, mask.size), dtype=torch.float64, pin_memory=True).numpy()
     torch.cuda.synchronize(dev)
     barrier()
     t0 = time.perf_counter()
@@ -455,7 +460,63 @@ def run_e2e(args, mask, nfluid, g, sy, dev):
             "d2h_bytes_per_step": round(2 * 4 * 8 * mask.size / nb, 3),
             "steps": nb, "lattice_steps": K,
             "what": "per model: lbm_create (host mask H2D) + lbm_step(lattice steps) + "
-                    "lbm_fields (rho,u D2H) + lbm_destroy, inside the timed region"}
+                    "lbm_fields (rho,u D2H into pinned host memory) + lbm_destroy, inside the "
+                    "timed region"}
+
+
+def run_precision_record(args):
+    """The precision workload's duct outside the timed region: D3Q27,
+    512 x 192 x 192 (191 x 191 fluid), Bn = 2, both models, FP32 and FP16
+    offset storage, each on the launch shape the tuner picks for it on this
+    geometry, timed with CUDA events over args.precision_steps lattice steps
+    after one check interval.  The FP16 velocity field is compared with the
+    FP32 one at the same step count (both from rest)."""
+    import torch
+    from paper_1610_01388_gb300 import autotune, lbm
+    from paper_1610_01388_gb300 import workloads as W
+    nx, ny, nz = 512, 192, 192
+    mask = W.duct_mask(nx, ny, nz)
+    nfluid = int((mask == 0).sum())
+    prm = W.duct_params(H=ny - 1, nu_p=NU_P, u_newton=0.02, bn=BN)
+    peak, kind = measured_hbm_peak()
+    st = torch.cuda.current_stream()
+    out, u_of = {}, {}
+    n = CHECK_EVERY + args.precision_steps
+    for storage in ("F32", "F16"):
+        for model in ("IR", "PR"):
+            shape = (256, 1)
+            if not args.no_tune:
+                shape, _ = autotune.tune("D3Q27", model, storage, mask.size, steps=100, mask=mask)
+            s = lbm.Solver("D3Q27", mask, model=model, storage=storage, mu_p=NU_P,
+                           sigma_y=prm["sigma_y"], m=M_PR, g=(prm["g"], 0.0, 0.0),
+                           check_every=CHECK_EVERY, use_torch=True)
+            s.step(CHECK_EVERY)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(st)
+            s.step(args.precision_steps)
+            e1.record(st)
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1) / 1e3 / args.precision_steps
+            b = s.info.bytes_per_fluid_update
+            _, u_of[(storage, model)] = s.fields()
+            s.close()
+            gbs = b * nfluid / t / 1e9
+            out[f"{model}/{storage}"] = {
+                "kernel": f"k_step<D3Q27,{model},{STORAGE_CTYPE[storage]}>",
+                "shape": f"{shape[0]}x{shape[1]}", "launch_us": round(t * 1e6, 2),
+                "mlups": round(nfluid / t / 1e6, 1), "bytes_per_fluid_update": b,
+                "achieved_gbs": round(gbs, 1), "frac": round(gbs / peak, 4)}
+    fl = mask == 0
+    diff = {}
+    for model in ("IR", "PR"):
+        a, r = u_of[("F16", model)][:, fl], u_of[("F32", model)][:, fl]
+        diff[model] = float(np.linalg.norm(a - r) / np.linalg.norm(r))
+    return {"workload": f"square duct D3Q27 {nx}x{ny}x{nz} ({ny - 1}x{nz - 1} fluid), Bn={BN:g}, "
+                        f"nu_p={NU_P}, PR m={M_PR:g}, from rest",
+            "fluid_cells": nfluid, "lattice_steps": n, "peak_gbs": peak,
+            "peak_kind": f"{kind} (copy bandwidth)", "kernels": out,
+            "rel_l2_u_f16_vs_f32_at_equal_steps": diff}
 
 
 def run_porous_record(args):
@@ -763,6 +824,8 @@ def main(argv=None):
     ap.add_argument("--porous-record", type=int, default=256, metavar="SIDE",
                     help="side of the porous box timed beside the duct (0 skips it)")
     ap.add_argument("--porous-steps", type=int, default=500)
+    ap.add_argument("--precision-steps", type=int, default=500,
+                    help="lattice steps timed on the precision workload's duct (0 skips it)")
     ap.add_argument("--serve-storage", default="F16,F32,mixed",
                     help="storage forms served, comma-separated, in order (mixed: FP16, with "
                          "FP32 for the near-jammed porous requests)")

@@ -158,6 +158,19 @@ lbm_status lbm_create_with_workspace(lbm_solver **out, lbm_lattice lat, int nx, 
  * long runs are replayed through captured CUDA graphs).  Asynchronous. */
 lbm_status lbm_step(lbm_solver *s, int64_t nsteps);
 
+/* One plain step taken in parts (no counterpart in the paper; it lets a
+ * z-slab update the planes that need no ghost values while its faces are in
+ * transit).  lbm_step_cells steps the cells cell_begin <= n < cell_end
+ * (0 <= cell_begin <= cell_end <= cells) from the current population buffer
+ * into the other one, with exactly the per-cell arithmetic of lbm_step;
+ * lbm_step_commit then makes the other buffer current and counts the step.
+ * The ranges given between two commits must cover every fluid cell once
+ * (a cell stepped twice would update the PR relaxation time twice).  Check
+ * steps are taken whole: both calls return LBM_EINVAL when the next step is
+ * a check step.  Asynchronous, on the solver's stream. */
+lbm_status lbm_step_cells(lbm_solver *s, int64_t cell_begin, int64_t cell_end);
+lbm_status lbm_step_commit(lbm_solver *s);
+
 /* Waits for all work enqueued on the solver's stream. */
 lbm_status lbm_sync(lbm_solver *s);
 

@@ -884,7 +884,13 @@ template <int MODEL, class S> __host__ __device__ constexpr bool copy_is_choice(
 // BLOCK: threads per block, chosen per (lattice, model, storage, size class)
 // by the tuning table; check steps always run with kBlock so their reduction
 // order does not depend on the tuning.
-template <class L, int MODEL, class S, bool CHECK, int BLOCK = kBlock, bool COPY = true>
+// RANGE: the launch covers cells [cell_begin, cell_end) only, one part of a
+// step taken in parts (lbm_step_cells; 256 threads, plain steps).  Its own
+// instantiation, so the whole-domain kernels carry no range arithmetic: under
+// the 48-register budget of the smaller lattices it made the D3Q19 FP32 PR
+// step spill and run 4 % slower.
+template <class L, int MODEL, class S, bool CHECK, int BLOCK = kBlock, bool COPY = true,
+          bool RANGE = false>
 __global__ void __launch_bounds__(BLOCK, step_min_blocks<L, MODEL, S, CHECK, BLOCK>())
 k_step(const KArgs a, const SrcPlanes<S> src, const DstPlanes<S> dst,
        const uint32_t* __restrict__ links, typename Store<S>::R* __restrict__ tau,
@@ -893,8 +899,8 @@ k_step(const KArgs a, const SrcPlanes<S> src, const DstPlanes<S> dst,
     static_assert(!CHECK || BLOCK == kBlock, "check steps use the fixed block size");
     using R = typename Store<S>::R;
     const KParams& kp = a.kp;
-    const int idx = blockIdx.x * BLOCK + threadIdx.x;
-    const bool inside = idx < kp.ncells;
+    const int idx = (RANGE ? kp.cell_begin : 0) + (int)(blockIdx.x * BLOCK + threadIdx.x);
+    const bool inside = idx < (RANGE ? kp.cell_end : kp.ncells);
     uint32_t rnd = 0u;
     if constexpr (Store<S>::kStochastic) {
         // this launch reads counter[parity] and leaves counter + 1 for the next
@@ -1399,7 +1405,8 @@ template <class L, int MODEL, class S, bool COPY>
 cudaError_t launch_step_c(bool check, const KParams& kp, const StepArgs& s, cudaStream_t st) {
     using R = typename Store<S>::R;
     const KArgs a = make_args<L>(kp);
-    const int grid = step_grid(kp.ncells);
+    const int ncell = kp.cell_end - kp.cell_begin;   // the cells this launch covers
+    const int grid = step_grid(ncell);
     const SrcPlanes<S> src = src_planes<L, S>(s.fsrc, kp.plane);
     const DstPlanes<S> dst = dst_planes<L, S>(s.fdst, kp.plane);
     const int block = (check || MODEL == kModelPRImplicit) ? kBlock : s.block;   // implicit: untuned
@@ -1417,12 +1424,16 @@ cudaError_t launch_step_c(bool check, const KParams& kp, const StepArgs& s, cuda
     if (check) {
         k_step<L, MODEL, S, true, kBlock, COPY><<<grid, kBlock, 0, st>>>(
             a, src, dst, s.links, (R*)s.tau, (R*)s.usnap, s.partials, s.rng_ctr, s.parity);
+    } else if (kp.cell_begin != 0 || kp.cell_end != kp.ncells) {
+        // one part of a step taken in parts (256 threads)
+        k_step<L, MODEL, S, false, kBlock, COPY, true><<<grid, kBlock, 0, st>>>(
+            a, src, dst, s.links, (R*)s.tau, (R*)s.usnap, s.partials, s.rng_ctr, s.parity);
     } else if constexpr (MODEL != kModelPRImplicit) {
         if (block == 128) {
-            k_step<L, MODEL, S, false, 128, COPY><<<(kp.ncells + 127) / 128, 128, 0, st>>>(
+            k_step<L, MODEL, S, false, 128, COPY><<<(ncell + 127) / 128, 128, 0, st>>>(
                 a, src, dst, s.links, (R*)s.tau, (R*)s.usnap, s.partials, s.rng_ctr, s.parity);
         } else if (block == 512) {
-            k_step<L, MODEL, S, false, 512, COPY><<<(kp.ncells + 511) / 512, 512, 0, st>>>(
+            k_step<L, MODEL, S, false, 512, COPY><<<(ncell + 511) / 512, 512, 0, st>>>(
                 a, src, dst, s.links, (R*)s.tau, (R*)s.usnap, s.partials, s.rng_ctr, s.parity);
         } else {
             k_step<L, MODEL, S, false, kBlock, COPY><<<grid, kBlock, 0, st>>>(

@@ -472,6 +472,8 @@ static lbm_status create_impl(lbm_solver** out, lbm_lattice lat, int nx, int ny,
     kp.ny = ny;
     kp.nz = nz;
     kp.ncells = s->ncells;
+    kp.cell_begin = 0;
+    kp.cell_end = s->ncells;
     kp.plane = s->lay.plane;
     kp.nu_p = p->mu_p;   // rho_0 = 1
     kp.sigma_y = p->sigma_y;
@@ -701,6 +703,54 @@ lbm_status lbm_step(lbm_solver* s, int64_t nsteps) {
             --left;
         }
     }
+    return LBM_OK;
+}
+
+lbm_status lbm_step_cells(lbm_solver* s, int64_t cell_begin, int64_t cell_end) {
+    lbm_status v = enter(s);
+    if (v != LBM_OK) return v;
+    if (cell_begin < 0 || cell_end < cell_begin || cell_end > s->ncells)
+        return fail(LBM_EINVAL, "cell range [%lld, %lld) is not within 0..%d", (long long)cell_begin,
+                    (long long)cell_end, s->ncells);
+    const int64_t k = s->p.check_every;
+    if (k > 0 && (s->steps + 1) % k == 0)
+        return fail(LBM_EINVAL, "the next step is a check step: take it whole with lbm_step");
+    if (cell_end == cell_begin) return LBM_OK;
+    KParams kp = s->kp;
+    kp.cell_begin = (int)cell_begin;
+    kp.cell_end = (int)cell_end;
+    StepArgs a;
+    a.fsrc = s->f[s->cur];
+    a.fdst = s->f[s->cur ^ 1];
+    a.links = s->links;
+    a.tau = s->tau;
+    a.usnap = s->usnap;
+    a.partials = s->partials;
+    a.rng_ctr = (uint32_t*)(s->stats + 2 * kNumStats);
+    a.parity = s->cur;
+    a.block = kBlock;
+    a.cpt = 1;
+    a.copy = s->copy;
+    const int km = kernel_model(s->p.model, s->kp.newton);
+    cudaError_t e;
+    switch (s->lat) {
+    case LBM_D2Q9: e = launch_step_D2Q9(km, s->p.storage, false, kp, a, s->stream); break;
+    case LBM_D3Q15: e = launch_step_D3Q15(km, s->p.storage, false, kp, a, s->stream); break;
+    case LBM_D3Q19: e = launch_step_D3Q19(km, s->p.storage, false, kp, a, s->stream); break;
+    default: e = launch_step_D3Q27(km, s->p.storage, false, kp, a, s->stream); break;
+    }
+    CK(s, e, "partial step launch");
+    return LBM_OK;
+}
+
+lbm_status lbm_step_commit(lbm_solver* s) {
+    lbm_status v = enter(s);
+    if (v != LBM_OK) return v;
+    const int64_t k = s->p.check_every;
+    if (k > 0 && (s->steps + 1) % k == 0)
+        return fail(LBM_EINVAL, "the next step is a check step: take it whole with lbm_step");
+    s->cur ^= 1;
+    s->steps += 1;
     return LBM_OK;
 }
 

@@ -32,6 +32,7 @@ struct KParams {
     uint32_t flags;
     int newton;           // PR: Newton iterations of the implicit tau update (0 = explicit)
     uint32_t hash_offset; // added to the cell index in the stochastic-rounding hash
+    int cell_begin, cell_end; // cells the single-domain step kernel covers (0, ncells)
     FastDiv div_nx, div_ny;   // idx -> (x, y, z) without integer division
 };
 

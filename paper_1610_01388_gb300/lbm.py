@@ -47,7 +47,7 @@ EXPORTED = ["lbm_params_default", "lbm_lattice_info", "lbm_workspace_bytes", "lb
             "lbm_tuning_set_batch_concurrency", "lbm_tuning_get_batch_concurrency",
             "lbm_tuning_set_batch_tile", "lbm_tuning_get_batch_tile",
             "lbm_halo_bytes", "lbm_halo_pack", "lbm_halo_unpack", "lbm_set_hash_offset",
-            "lbm_check_sums"]
+            "lbm_check_sums", "lbm_step_cells", "lbm_step_commit"]
 LBM_REQ_QUEUED, LBM_REQ_RUNNING, LBM_REQ_CONVERGED, LBM_REQ_CAPPED, LBM_REQ_FAILED = range(5)
 LBM_STEADY_FLOW, LBM_STEADY_RESIDUAL = 0, 1
 
@@ -164,6 +164,8 @@ def library():
             "lbm_halo_unpack": [vp, i32, vp],
             "lbm_set_hash_offset": [vp, i64],
             "lbm_check_sums": [vp, vp, P(d), P(d)],
+            "lbm_step_cells": [vp, i64, i64],
+            "lbm_step_commit": [vp],
             "lbm_tuning_get_batch_tile": [i32, i32, i32, i64, P(i32), P(i32), P(i32)],
             "lbm_get_wait_limit": [P(d)],
         }
@@ -445,6 +447,14 @@ def lbm_check_sums(h):
     du2, u2 = ctypes.c_double(), ctypes.c_double()
     _check(library().lbm_check_sums(h, us, ctypes.byref(du2), ctypes.byref(u2)))
     return np.array(list(us)), du2.value, u2.value
+
+
+def lbm_step_cells(h, cell_begin, cell_end):
+    _check(library().lbm_step_cells(h, int(cell_begin), int(cell_end)))
+
+
+def lbm_step_commit(h):
+    _check(library().lbm_step_commit(h))
 
 
 def lbm_set_wait_limit(seconds):

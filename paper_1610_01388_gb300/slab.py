@@ -24,7 +24,9 @@ The pieces:
                  rates and residuals.
 The rings and SlabDomain use only a stepper's pack(side), unpack(side, buf),
 empty_face(), step(), sums() and flow_sums(), so any stepper with that
-interface is decomposed the same way.
+interface is decomposed the same way; a stepper that also takes a step in
+parts (step_inner, step_faces, next_is_check) gets the exchange overlapped
+with the update of its inner planes.
 """
 from __future__ import annotations
 
@@ -85,6 +87,24 @@ class GpuSlab:
     def step(self, n=1):
         self.solver.step(n)
 
+    def next_is_check(self):
+        k = self.solver.params.check_every
+        return k > 0 and (lbm.lbm_get_info(self.solver.h).steps_done + 1) % k == 0
+
+    def step_inner(self):
+        """The planes that read no ghost value (interior planes 2..nz_local-1)."""
+        nxy = self.nx * self.ny
+        if self.nz_local > 2:
+            lbm.lbm_step_cells(self.solver.h, 2 * nxy, self.nz_local * nxy)
+
+    def step_faces(self):
+        """The two interior planes next to the faces, then the buffer flip."""
+        nxy = self.nx * self.ny
+        lbm.lbm_step_cells(self.solver.h, nxy, 2 * nxy)
+        if self.nz_local > 1:
+            lbm.lbm_step_cells(self.solver.h, self.nz_local * nxy, (self.nz_local + 1) * nxy)
+        lbm.lbm_step_commit(self.solver.h)
+
     def sync(self):
         self.solver.sync()
 
@@ -118,9 +138,15 @@ class LocalRing:
         self.slabs = list(slabs)
 
     def exchange(self):
+        self.exchange_begin()
+        self.exchange_end()
+
+    def exchange_begin(self):
+        self._faces = ([s.pack(1) for s in self.slabs], [s.pack(0) for s in self.slabs])
+
+    def exchange_end(self):
+        up, down = self._faces
         n = len(self.slabs)
-        up = [s.pack(1) for s in self.slabs]
-        down = [s.pack(0) for s in self.slabs]
         for k, s in enumerate(self.slabs):
             s.unpack(0, up[(k - 1) % n])     # the lower neighbour's upward populations
             s.unpack(1, down[(k + 1) % n])   # the upper neighbour's downward populations
@@ -147,10 +173,15 @@ class RankRing:
         self._recv = [slab.empty_face(), slab.empty_face()]
 
     def exchange(self):
+        self.exchange_begin()
+        self.exchange_end()
+
+    def exchange_begin(self):
+        """Pack both faces and start their transfer (returns at once)."""
         up, down = self.slab.pack(1), self.slab.pack(0)
+        self._reqs = None
         if self.world == 1:
-            self.slab.unpack(0, up)
-            self.slab.unpack(1, down)
+            self._local = (up, down)
             return
         d = self.dist
         above, below = (self.rank + 1) % self.world, (self.rank - 1) % self.world
@@ -163,8 +194,18 @@ class RankRing:
                d.P2POp(d.irecv, self._recv[0], peer(below), self.group, 0),
                d.P2POp(d.isend, down, peer(below), self.group, 1),
                d.P2POp(d.irecv, self._recv[1], peer(above), self.group, 1)]
-        for r in d.batch_isend_irecv(ops):
+        self._reqs = d.batch_isend_irecv(ops)
+
+    def exchange_end(self):
+        """Wait for the faces and write them into the ghost planes."""
+        if self._reqs is None:
+            up, down = self._local
+            self.slab.unpack(0, up)
+            self.slab.unpack(1, down)
+            return
+        for r in self._reqs:
             r.wait()
+        self._reqs = None
         self.slab.unpack(0, self._recv[0])
         self.slab.unpack(1, self._recv[1])
 
@@ -193,10 +234,22 @@ class SlabDomain:
         self.nz, self.ny, self.nx = nz, ny, nx
 
     def step(self, n=1):
+        """n steps.  A plain step, when every slab can take one in parts,
+        overlaps the face exchange with the update of the planes that read
+        no ghost value; a check step exchanges first and steps whole."""
         for _ in range(int(n)):
-            self.ring.exchange()
-            for s in self.ring.slabs:
-                s.step(1)
+            slabs = self.ring.slabs
+            if all(hasattr(s, "step_inner") and not s.next_is_check() for s in slabs):
+                self.ring.exchange_begin()
+                for s in slabs:
+                    s.step_inner()
+                self.ring.exchange_end()
+                for s in slabs:
+                    s.step_faces()
+            else:
+                self.ring.exchange()
+                for s in slabs:
+                    s.step(1)
 
     def check_sums(self):
         """(sum of u_real [3], sum |u - u_prev|^2, sum |u|^2) over the whole

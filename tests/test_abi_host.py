@@ -117,6 +117,8 @@ def test_halo_calls_reject_null_handle():
     assert lib.lbm_halo_unpack(None, 1, None) == lbm.LBM_EINVAL
     assert lib.lbm_set_hash_offset(None, 5) == lbm.LBM_EINVAL
     assert lib.lbm_check_sums(None, None, None, None) == lbm.LBM_EINVAL
+    assert lib.lbm_step_cells(None, 0, 1) == lbm.LBM_EINVAL
+    assert lib.lbm_step_commit(None) == lbm.LBM_EINVAL
 
 
 def test_create_rejects_empty_and_oversized_extents():

@@ -53,3 +53,25 @@ def test_recorded_traffic_only_for_the_captured_workload(monkeypatch):
     monkeypatch.setattr(bench, "POROUS", 0)
     monkeypatch.setattr(bench, "KERNEL_FINGERPRINT", "0" * 16)
     assert bench.ncu_traffic(*key) is None
+
+
+def test_mixed_storage_routes_near_jammed_porous_requests_to_fp32():
+    reqs = W.serving_requests(n=60, rate=1e9, seed=7, storage="F16", channel_widths=(16, 20),
+                              duct_sides=(16, 18), duct_length=8, porous_sides=(24, 24),
+                              porous_radius=(3.0, 4.0))
+    got = [bench._route("mixed", r) for r in reqs]
+    for r, st in zip(reqs, got):
+        want = "F32" if (r["kind"] == "porous" and r["bn"] >= 1.0) else "F16"
+        assert st == want
+    assert "F32" in got and "F16" in got
+    assert bench._route("mixed", None) == "F16"
+    assert bench._route("F32", reqs[0]) == "F32"
+
+
+def test_gpus_must_match_world_size(monkeypatch, capsys):
+    import pytest
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    with pytest.raises(SystemExit) as e:
+        bench.main(["--gpus", "4"])
+    assert e.value.code == 2
+    assert "WORLD_SIZE=2" in capsys.readouterr().err

@@ -57,3 +57,72 @@ def test_halo_calls_reject_solvers_without_ghosts():
     assert lib.lbm_halo_unpack(g.h, 0, None) == lbm.LBM_EINVAL
     assert lbm.lbm_halo_bytes(g.h) == 5 * 8 * 6 * 4        # D3Q19: 5 crossing populations, FP32
     g.close()
+
+
+@pytest.mark.parametrize("storage,model", [("F32", "PR"), ("F16", "PR"), ("F64", "IR"),
+                                           ("BF16", "IR")])
+def test_step_in_parts_equals_whole_step(storage, model):
+    """A plain step taken as three cell ranges (cut anywhere, not at warp or
+    plane boundaries) plus the commit equals lbm_step(1) bit for bit, the
+    16-bit forms' stochastic rounding included; check steps are refused."""
+    mask, _ = W.porous_mask(24, porosity=0.7, r_min=3.0, r_max=4.0, seed=5)
+    prm = dict(model=model, storage=storage, mu_p=0.1, sigma_y=2e-6, m=1e6, g=(2e-5, 0.0, 0.0),
+               check_every=10)
+    a = lbm.Solver("D3Q19", mask, use_torch=True, **prm)
+    b = lbm.Solver("D3Q19", mask, use_torch=True, **prm)
+    n = mask.size
+    cuts = [0, 1237, 8191, n]
+    for step in range(1, 26):
+        a.step(1)
+        if step % 10 == 0:
+            with pytest.raises(lbm.LbmError):
+                lbm.lbm_step_cells(b.h, 0, n)
+            with pytest.raises(lbm.LbmError):
+                lbm.lbm_step_commit(b.h)
+            b.step(1)
+        else:
+            for c0, c1 in zip(cuts[:-1], cuts[1:]):
+                lbm.lbm_step_cells(b.h, c0, c1)
+            lbm.lbm_step_commit(b.h)
+    assert np.array_equal(a.get_populations(), b.get_populations())
+    if model == "PR":
+        assert np.array_equal(a.get_tau(), b.get_tau())
+    assert a.residual() == b.residual()
+    lib = lbm.library()
+    assert lib.lbm_step_cells(b.h, -1, 5) == lbm.LBM_EINVAL
+    assert lib.lbm_step_cells(b.h, 10, 5) == lbm.LBM_EINVAL
+    assert lib.lbm_step_cells(b.h, 0, n + 1) == lbm.LBM_EINVAL
+    a.close()
+    b.close()
+
+
+def test_rank_ring_on_one_nccl_rank():
+    """The rank form of the decomposition on this GPU as a one-rank NCCL
+    group: the slab's faces come back to itself (periodic), its sums go
+    through an NCCL allreduce of device tensors, and it must equal the
+    undivided solver bit for bit."""
+    import os
+    import socket
+    import torch
+    import torch.distributed as dist
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    os.environ.update({"MASTER_ADDR": "127.0.0.1", "MASTER_PORT": str(port)})
+    dist.init_process_group("nccl", rank=0, world_size=1, device_id=torch.device("cuda", 0))
+    try:
+        mask, _ = W.porous_mask(24, porosity=0.7, r_min=3.0, r_max=4.0, seed=9)
+        prm = dict(model="PR", storage="F32", mu_p=0.1, sigma_y=2e-6, m=1e6, g=(2e-5, 0.0, 0.0),
+                   check_every=20)
+        dom = slab.gpu_rank_slab("D3Q19", mask, **prm)
+        ref = lbm.Solver("D3Q19", mask, use_torch=True, **prm)
+        dom.step(50)
+        ref.step(50)
+        s = dom.ring.slabs[0]
+        assert np.array_equal(s.populations(), ref.get_populations())
+        assert abs(dom.flowrate(0) - ref.flowrate(0)) <= 1e-12 * abs(ref.flowrate(0))
+        assert abs(dom.residual() - ref.residual()[0]) <= 1e-10 * ref.residual()[0]
+        s.close()
+        ref.close()
+    finally:
+        dist.destroy_process_group()
