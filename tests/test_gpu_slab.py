@@ -5,7 +5,8 @@ nearest neighbours (eq. 8), so the slabs' populations must equal the
 undivided solver's bit for bit (same per-cell arithmetic; the 16-bit form
 draws the same stochastic-rounding bits through the hash offset), and the
 flow rate and residual combined from the slabs must equal the undivided
-ones to round-off of their summation order."""
+ones to round-off of their summation order (the check step's warp and block
+sums run in the arithmetic type, FP32 for the FP32 and 16-bit forms)."""
 import numpy as np
 import pytest
 
@@ -36,7 +37,8 @@ def test_slabs_match_undivided_domain(lat, model, storage, nslabs):
         assert abs(dom.flowrate(a) - q) <= 1e-12 * abs(q) + 1e-18, a
     r_ref, at, _ = ref.residual()
     assert at == 100
-    assert abs(dom.residual() - r_ref) <= 1e-10 * r_ref
+    # FP32 warp and block sums in the check step, grouped by slab (FP64 for F64)
+    assert abs(dom.residual() - r_ref) <= (1e-12 if storage == "F64" else 1e-6) * r_ref
     _, u = dom.fields()
     _, u_ref = ref.fields()
     assert np.array_equal(u, u_ref)
@@ -59,15 +61,38 @@ def test_halo_calls_reject_solvers_without_ghosts():
     g.close()
 
 
-@pytest.mark.parametrize("storage,model", [("F32", "PR"), ("F16", "PR"), ("F64", "IR"),
-                                           ("BF16", "IR")])
-def test_step_in_parts_equals_whole_step(storage, model):
+@pytest.mark.parametrize("nslabs", [6, 3])
+def test_thin_slabs(nslabs):
+    """Slabs one and two planes deep (no inner planes; both planes next to a
+    face) still match the undivided domain bit for bit, with check steps."""
+    mask, _ = W.porous_mask((24, 20, 6), porosity=0.7, r_min=2.0, r_max=3.0, seed=4)   # nx, ny, nz
+    prm = dict(model="IR", storage="F32", mu_p=0.1, sigma_y=2e-6, g=(2e-5, 1e-6, 3e-6),
+               check_every=7)
+    dom = slab.gpu_slab_domain("D3Q27", mask, nslabs, **prm)
+    ref = lbm.Solver("D3Q27", mask, use_torch=True, **prm)
+    dom.step(30)
+    ref.step(30)
+    f_ref = ref.get_populations()
+    for (z0, nl, _), s in zip(slab.split_z(mask, nslabs), dom.ring.slabs):
+        assert np.array_equal(s.populations(), f_ref[:, z0:z0 + nl])
+    # the check step sums warps and blocks in FP32 (FP64 per-block partials):
+    # other slab boundaries group those sums differently
+    assert abs(dom.residual() - ref.residual()[0]) <= 1e-6 * ref.residual()[0]
+    for s in dom.ring.slabs:
+        s.close()
+    ref.close()
+
+
+@pytest.mark.parametrize("storage,model,newton", [("F32", "PR", 0), ("F16", "PR", 0),
+                                                  ("F64", "IR", 0), ("BF16", "IR", 0),
+                                                  ("F64", "PR", 3)])
+def test_step_in_parts_equals_whole_step(storage, model, newton):
     """A plain step taken as three cell ranges (cut anywhere, not at warp or
     plane boundaries) plus the commit equals lbm_step(1) bit for bit, the
     16-bit forms' stochastic rounding included; check steps are refused."""
     mask, _ = W.porous_mask(24, porosity=0.7, r_min=3.0, r_max=4.0, seed=5)
     prm = dict(model=model, storage=storage, mu_p=0.1, sigma_y=2e-6, m=1e6, g=(2e-5, 0.0, 0.0),
-               check_every=10)
+               check_every=10, newton_iters=newton)
     a = lbm.Solver("D3Q19", mask, use_torch=True, **prm)
     b = lbm.Solver("D3Q19", mask, use_torch=True, **prm)
     n = mask.size
@@ -121,7 +146,7 @@ def test_rank_ring_on_one_nccl_rank():
         s = dom.ring.slabs[0]
         assert np.array_equal(s.populations(), ref.get_populations())
         assert abs(dom.flowrate(0) - ref.flowrate(0)) <= 1e-12 * abs(ref.flowrate(0))
-        assert abs(dom.residual() - ref.residual()[0]) <= 1e-10 * ref.residual()[0]
+        assert abs(dom.residual() - ref.residual()[0]) <= 1e-6 * ref.residual()[0]
         s.close()
         ref.close()
     finally:
