@@ -108,12 +108,10 @@ def workload_mask(nx=None):
 # profiles/ summaries).  NCU_TRAFFIC: the 256x128x128 D3Q27 duct, keyed by
 # storage, model, block size and cells per thread.  NCU_TRAFFIC_POROUS: the
 # porous box of the porous record (256^3, D3Q19, 256 threads), keyed by
-# storage and model.  Both are valid only
+# layout, storage and model.  Both are valid only
 # for the device-code sources they were captured with (KERNEL_FINGERPRINT)
 # and are reported as null once any of those sources changes.
-NCU_TRAFFIC_POROUS = {
-    ("F16", "IR"): 1306262982, ("F16", "PR"): 1435169166, ("F32", "IR"): 2569450785, ("F32", "PR"): 2696842270,
-}
+NCU_TRAFFIC_POROUS = {}
 NCU_TRAFFIC = {
     ("F32", "IR", 128, 1): 855828959, ("F32", "IR", 128, 2): 855420895, ("F32", "IR", 256, 1): 855586898, ("F32", "IR", 256, 2): 857031687, ("F32", "IR", 512, 1): 857374821,
     ("F32", "PR", 128, 1): 889919270, ("F32", "PR", 128, 2): 889816892, ("F32", "PR", 256, 1): 889681265, ("F32", "PR", 256, 2): 890840825, ("F32", "PR", 512, 1): 890229380,
@@ -140,13 +138,13 @@ def kernel_fingerprint():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(storage, model, block, cpt, override=None, workload="duct"):
+def ncu_traffic(storage, model, block, cpt, override=None, workload="duct", layout="dense"):
     if override is not None:
         return override
     if KERNEL_FINGERPRINT is None or kernel_fingerprint() != KERNEL_FINGERPRINT:
         return None
     if workload == "porous":
-        return NCU_TRAFFIC_POROUS.get((storage, model))
+        return NCU_TRAFFIC_POROUS.get((layout, storage, model))
     if POROUS or (LATTICE, NX, NY, NZ) != ("D3Q27", 256, 128, 128):
         return None
     return NCU_TRAFFIC.get((storage, model, block, cpt))
@@ -524,9 +522,11 @@ def run_porous_record(args):
     box of random non-overlapping spheres (radius 6-10, porosity 0.7, seed 1),
     D3Q19, both models, FP32 and FP16 storage, each timed with CUDA events
     over args.porous_steps lattice steps after one check interval of warm-up.
-    The dense layout keeps every cell, so a warp with any fluid cell moves
-    all 32 cells' populations: touched_over_fluid is that floor of the
-    traffic relative to the algorithmic (fluid-cell) bytes."""
+    The compact layout (fluid cells only) is the porous path; the dense
+    layout is timed beside it.  The dense layout keeps every cell, so an
+    aligned group of 8 cells (one 32-byte sector of a plane) with any fluid
+    cell moves all 8 cells' populations: touched_over_fluid is that floor of
+    its traffic relative to the algorithmic (fluid-cell) bytes."""
     import torch
     from paper_1610_01388_gb300 import lbm
     from paper_1610_01388_gb300 import workloads as W
@@ -534,42 +534,47 @@ def run_porous_record(args):
     mask, info = W.porous_mask(side, porosity=0.7, r_min=6.0, r_max=10.0, seed=1)
     flat = (mask.reshape(-1) == 0).astype(np.int64)
     nfluid = int(flat.sum())
-    warp = np.arange(flat.size) // 32
-    fluid_per_warp = np.bincount(warp, weights=flat)
-    cells_per_warp = np.bincount(warp)
-    touched = int(cells_per_warp[fluid_per_warp > 0].sum())
+    group = np.arange(flat.size) // 8
+    fluid_per_group = np.bincount(group, weights=flat)
+    cells_per_group = np.bincount(group)
+    touched = int(cells_per_group[fluid_per_group > 0].sum())
     prm = W.porous_params(nu_p=NU_P, d_mean=16.0, g=2e-5, bn=BN)
     peak, kind = measured_hbm_peak()
     st = torch.cuda.current_stream()
-    kernels = {}
-    for storage in ("F32", "F16"):
-        for model in ("IR", "PR"):
-            s = lbm.Solver("D3Q19", mask, model=model, storage=storage, mu_p=NU_P,
-                           sigma_y=prm["sigma_y"], m=M_PR, g=(prm["g"], 0.0, 0.0),
-                           check_every=CHECK_EVERY, use_torch=True)
-            s.step(CHECK_EVERY)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            torch.cuda.synchronize()
-            e0.record(st)
-            s.step(args.porous_steps)
-            e1.record(st)
-            torch.cuda.synchronize()
-            t = e0.elapsed_time(e1) / 1e3 / args.porous_steps
-            b = s.info.bytes_per_fluid_update
-            s.residual()
-            s.close()
-            gbs = b * nfluid / t / 1e9
-            kernels[f"{model}/{storage}"] = {
-                "kernel": f"k_step<D3Q19,{model},{STORAGE_CTYPE[storage]}>",
-                "launch_us": round(t * 1e6, 2), "mlups": round(nfluid / t / 1e6, 1),
-                "bytes_per_fluid_update": b, "achieved_gbs": round(gbs, 1),
-                "frac": round(gbs / peak, 4),
-                "frac_of_touched": round(gbs * touched / nfluid / peak, 4),
-                "traffic": ncu_traffic(storage, model, 256, 1, None, workload="porous")}
+    kernels = {"compact": {}, "dense": {}}
+    for layout in ("compact", "dense"):
+        for storage in ("F32", "F16"):
+            for model in ("IR", "PR"):
+                s = lbm.Solver("D3Q19", mask, model=model, storage=storage, mu_p=NU_P,
+                               sigma_y=prm["sigma_y"], m=M_PR, g=(prm["g"], 0.0, 0.0),
+                               check_every=CHECK_EVERY, use_torch=True, layout=layout)
+                s.step(CHECK_EVERY)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record(st)
+                s.step(args.porous_steps)
+                e1.record(st)
+                torch.cuda.synchronize()
+                t = e0.elapsed_time(e1) / 1e3 / args.porous_steps
+                b = s.info.bytes_per_fluid_update
+                s.residual()
+                s.close()
+                gbs = b * nfluid / t / 1e9
+                name = "k_step_compact" if layout == "compact" else "k_step"
+                k = {"kernel": f"{name}<D3Q19,{model},{STORAGE_CTYPE[storage]}>",
+                     "launch_us": round(t * 1e6, 2), "mlups": round(nfluid / t / 1e6, 1),
+                     "bytes_per_fluid_update": b, "achieved_gbs": round(gbs, 1),
+                     "frac": round(gbs / peak, 4),
+                     "traffic": ncu_traffic(storage, model, 256, 1, None, workload="porous",
+                                            layout=layout)}
+                if layout == "dense":
+                    k["frac_of_touched"] = round(gbs * touched / nfluid / peak, 4)
+                kernels[layout][f"{model}/{storage}"] = k
     roof = {}
+    comp = kernels["compact"]
     for storage in ("F32", "F16"):
-        dom = max(("IR", "PR"), key=lambda m: kernels[f"{m}/{storage}"]["launch_us"])
-        k = kernels[f"{dom}/{storage}"]
+        dom = max(("IR", "PR"), key=lambda m: comp[f"{m}/{storage}"]["launch_us"])
+        k = comp[f"{dom}/{storage}"]
         roof[storage] = {"bound": "hbm", "kernel": k["kernel"] + " (dominant by time)",
                          "achieved": k["achieved_gbs"], "peak": peak,
                          "peak_kind": f"{kind} (copy bandwidth)", "unit": "GB/s",
@@ -580,9 +585,11 @@ def run_porous_record(args):
                         f"6-10, porosity {info['porosity']:.3f}, seed 1), Bn={BN:g} a priori, "
                         f"nu_p={NU_P}, PR m={M_PR:g}; 256 threads per block, check step every "
                         f"{CHECK_EVERY}",
+            "layout": "compact (fluid cells only, LBM_FLAG_COMPACT); dense timed beside it",
             "fluid_cells": nfluid, "cells": int(flat.size),
             "touched_over_fluid": round(touched / nfluid, 4),
-            "lattice_steps_timed": args.porous_steps, "roofline": roof, "kernels": kernels}
+            "lattice_steps_timed": args.porous_steps, "roofline": roof,
+            "kernels": kernels["compact"], "dense": kernels["dense"]}
 
 
 # --- serving ----------------------------------------------------------------------

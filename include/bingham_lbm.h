@@ -102,6 +102,22 @@ typedef enum {
                                    counted, and their mask rows are the neighbours'
                                    own rows, so bounce-back across the slab faces is
                                    that of the whole domain.  3D lattices, nz >= 3 */
+#define LBM_FLAG_COMPACT 0x4u   /* compact layout (no counterpart in the paper; for
+                                   domains with many solid cells, e.g. porous media):
+                                   the populations, link words, PR tau and check-step
+                                   snapshot are held for the fluid cells only, one
+                                   slot each in cell-index order, and one thread steps
+                                   one slot.  The step's per-cell arithmetic is that
+                                   of the dense layout (its own kernel, so the same to
+                                   round-off of the arithmetic type: the compiler may
+                                   contract multiply-adds differently).  On a porous
+                                   medium it moves the fluid cells' bytes only.  Solid
+                                   cells hold nothing:
+                                   they read back as the rest state (populations w_i,
+                                   tau at its initial value) and uploads to them are
+                                   dropped.  Not with LBM_FLAG_Z_GHOSTS, not in
+                                   batches (LBM_EINVAL); lbm_step_cells and
+                                   lbm_step_commit return LBM_EINVAL */
 
 /* Rheology, forcing and run-control parameters (lattice units, rho_0 = 1). */
 typedef struct {
@@ -136,9 +152,17 @@ lbm_status lbm_lattice_info(lbm_lattice lat, int *Q, int *D, int *c, double *w);
 
 /* Device bytes lbm_create_with_workspace needs for this problem (populations
  * A/B, link masks, the PR relaxation-time field (one, updated in place),
- * residual snapshot, reduction partials). */
+ * residual snapshot, reduction partials).  With LBM_FLAG_COMPACT the size
+ * depends on the fluid cells: this is then an upper bound (every cell fluid);
+ * lbm_workspace_bytes_for_mask gives the exact size. */
 lbm_status lbm_workspace_bytes(lbm_lattice lat, int nx, int ny, int nz,
                                const lbm_params *p, size_t *bytes);
+
+/* The same for a given solid mask (validated as by lbm_create): exact for
+ * both layouts.  Host only. */
+lbm_status lbm_workspace_bytes_for_mask(lbm_lattice lat, int nx, int ny, int nz,
+                                        const uint8_t *solid_mask, const lbm_params *p,
+                                        size_t *bytes);
 
 /* Creates a solver at rest (f_i = w_i, rho = 1, u = 0; PR tau = 1/2 + 3 nu_0,
  * nu_0 = nu_p + m sigma_y).  solid_mask: host, nx*ny*nz bytes, nonzero =
@@ -217,8 +241,8 @@ lbm_status lbm_residual(lbm_solver *s, double *residual, int64_t *at_step, doubl
 /* Replace / read the population state (host, FP64 full f, Q*N, library
  * order).  lbm_set_populations writes both A/B buffers, so a solid cell
  * keeps the uploaded populations through every later step (a step defines
- * nothing for solid cells) and lbm_get_populations returns them.
- * Synchronises. */
+ * nothing for solid cells) and lbm_get_populations returns them (compact
+ * layout: solid cells are not held and read back as w_i).  Synchronises. */
 lbm_status lbm_set_populations(lbm_solver *s, const double *f);
 lbm_status lbm_get_populations(lbm_solver *s, double *f);
 
@@ -232,7 +256,9 @@ lbm_status lbm_get_populations_cells(lbm_solver *s, const int64_t *cells, int64_
 
 /* PR relaxation-time field tau = 1/2 + 3 nu_app (eq. tau_visc), one value per
  * cell (host, N doubles), the value the next step's strain rate uses
- * (eq. LBM_strain_rate).  LBM_EINVAL for IR.  Synchronises. */
+ * (eq. LBM_strain_rate).  Compact layout: solid cells' values are dropped on
+ * upload and read back as the initial 1/2 + 3 nu_0.  LBM_EINVAL for IR.
+ * Synchronises. */
 lbm_status lbm_set_tau(lbm_solver *s, const double *tau);
 lbm_status lbm_get_tau(lbm_solver *s, double *tau);
 

@@ -28,6 +28,7 @@
 // previous snapshot into per-block partials, summed in FP64 in a fixed order.
 #pragma once
 
+#include <algorithm>
 #include <cstdint>
 #include <type_traits>
 #include <utility>
@@ -378,26 +379,11 @@ __device__ __forceinline__ void cell_xyz(const KParams& kp, int idx, int& x, int
 #ifndef BLBM_WARP_UNIFORM_GATHER
 #define BLBM_WARP_UNIFORM_GATHER 1
 #endif
-// self = true loads the cell's own populations, plane by plane (all offsets
-// 0; lk must be 0): the copy-through of a solid cell.
-template <class L, class S, class Src>
-__device__ __forceinline__ void gather(const KParams& kp, const Src& P, uint32_t lk,
-                                       int idx, typename Store<S>::R (&v)[L::Q],
-                                       bool self = false) {
-    const int nx = kp.nx, ny = kp.ny, nz = kp.nz;
-    int x, y, z;
-    cell_xyz(kp, idx, x, y, z);
-    // offsets from idx to the source cell x - c for c = +1 (m) and c = -1 (p)
-    const int sy = nx, sz = nx * ny;
-    int dxm = (x == 0) ? nx - 1 : -1;
-    int dxp = (x == nx - 1) ? -(nx - 1) : 1;
-    int dym = (y == 0) ? (ny - 1) * sy : -sy;
-    int dyp = (y == ny - 1) ? -(ny - 1) * sy : sy;
-    int dzm = (z == 0) ? (nz - 1) * sz : -sz;
-    int dzp = (z == nz - 1) ? -(nz - 1) * sz : sz;
-    if (self) dxm = dxp = dym = dyp = dzm = dzp = 0;
-    auto offset = [&](auto I) {
-        constexpr int i = decltype(I)::value;
+// Offsets from a cell's index to its pull sources x - c (periodic wrap):
+// m for a velocity component +1, p for -1.
+struct PullOffsets {
+    int dxm, dxp, dym, dyp, dzm, dzp;
+    template <class L, int i> __device__ __forceinline__ int of() const {
         constexpr int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
         int off = 0;
         if constexpr (cx > 0) off += dxm;
@@ -407,7 +393,33 @@ __device__ __forceinline__ void gather(const KParams& kp, const Src& P, uint32_t
         if constexpr (cz > 0) off += dzm;
         if constexpr (cz < 0) off += dzp;
         return off;
-    };
+    }
+};
+
+__device__ __forceinline__ PullOffsets pull_offsets(const KParams& kp, int idx) {
+    const int nx = kp.nx, ny = kp.ny, nz = kp.nz;
+    int x, y, z;
+    cell_xyz(kp, idx, x, y, z);
+    const int sy = nx, sz = nx * ny;
+    PullOffsets o;
+    o.dxm = (x == 0) ? nx - 1 : -1;
+    o.dxp = (x == nx - 1) ? -(nx - 1) : 1;
+    o.dym = (y == 0) ? (ny - 1) * sy : -sy;
+    o.dyp = (y == ny - 1) ? -(ny - 1) * sy : sy;
+    o.dzm = (z == 0) ? (nz - 1) * sz : -sz;
+    o.dzp = (z == nz - 1) ? -(nz - 1) * sz : sz;
+    return o;
+}
+
+// self = true loads the cell's own populations, plane by plane (all offsets
+// 0; lk must be 0): the copy-through of a solid cell.
+template <class L, class S, class Src>
+__device__ __forceinline__ void gather(const KParams& kp, const Src& P, uint32_t lk,
+                                       int idx, typename Store<S>::R (&v)[L::Q],
+                                       bool self = false) {
+    PullOffsets o = pull_offsets(kp, idx);
+    if (self) o = PullOffsets{0, 0, 0, 0, 0, 0};
+    auto offset = [&](auto I) { return o.template of<L, decltype(I)::value>(); };
     // The path is chosen per warp: a warp takes the plain pull only when none
     // of its cells has a solid neighbour.  A per-thread choice makes a warp
     // that mixes wall and interior cells run both paths one after the other,
@@ -806,14 +818,48 @@ template <class L, int MODEL, class S, bool CHECK, int BLOCK> constexpr int step
     return 1280 / BLOCK;
 }
 
+// Stores one cell's outgoing populations at element n of the planes: the
+// rest population, then the opposite pairs (i, i + 1), one random word each.
+template <class L, class S, class Dst>
+__device__ __forceinline__ void store_cell(const Dst& dst, int n,
+                                           const typename Store<S>::R (&f)[L::Q], uint32_t rnd) {
+    Store<S>::template st<L, 0>(dst.template at<0>(n), f[0], rnd);
+    static_for<0, (L::Q - 1) / 2>([&](auto P) {
+        constexpr int i = 2 * decltype(P)::value + 1;
+        Store<S>::template st2<L, i>(dst.template at<i>(n), dst.template at<i + 1>(n), f[i],
+                                     f[i + 1], pair_bits<decltype(P)::value + 1>(rnd));
+    });
+}
+
+// A cell's check-step contributions (velocity, its change since the previous
+// snapshot up, density offset, non-finite flag); its velocity becomes element
+// n of the snapshot.
+template <class R>
+__device__ __forceinline__ void check_stats(const R (&ur)[3], const R (&up)[3], R drho,
+                                            R* __restrict__ usnap, int64_t plane, int n,
+                                            R (&acc)[kNumStats]) {
+    R du2 = R(0), u2 = R(0);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        acc[kStatUx + d] = ur[d];
+        du2 += (ur[d] - up[d]) * (ur[d] - up[d]);
+        u2 += ur[d] * ur[d];
+        usnap[(int64_t)d * plane + n] = ur[d];
+    }
+    acc[kStatDu2] = du2;
+    acc[kStatU2] = u2;
+    acc[kStatDrho] = drho;
+    acc[kStatNonFinite] = isfinite(drho) ? R(0) : R(1);
+}
+
 // One cell of one time step: pull, collide, store; on check steps the cell's
 // contributions to the flow-rate and residual sums go to acc.  Shared by the
 // single-domain and the batched kernels so both do identical arithmetic.
-// fluid = false (plain steps only) copies a solid cell's populations through
-// unchanged, the step's definition for solid cells: a warp that holds fluid
-// cells then writes whole 32-byte sectors.  A sector the stores cover only in
-// part costs a DRAM read before its write; at the edges of a porous medium's
-// grains that doubled the reads.
+// fluid = false copies a solid cell's populations through unchanged, the
+// step's definition for solid cells: the stores of a group of cells that
+// holds fluid cells then fill whole 32-byte sectors.  A sector the stores
+// cover only in part costs a DRAM read before its write; at the edges of a
+// porous medium's grains that doubled the reads.
 template <class L, int MODEL, class S, bool CHECK, class Src, class Dst>
 __device__ __forceinline__ void cell_step(const KParams& kp, const Coef<typename Store<S>::R>& c,
                                           const Src& src, const Dst& dst, uint32_t lk, int idx,
@@ -842,33 +888,18 @@ __device__ __forceinline__ void cell_step(const KParams& kp, const Coef<typename
             collide_ir<L, S>(c, kp.flags, f, drho, ur);
         }
     }
-    // rest population, then opposite pairs (i, i + 1), one random word each
-    Store<S>::template st<L, 0>(dst.template at<0>(idx), f[0], rnd);
-    static_for<0, (L::Q - 1) / 2>([&](auto P) {
-        constexpr int i = 2 * decltype(P)::value + 1;
-        Store<S>::template st2<L, i>(dst.template at<i>(idx), dst.template at<i + 1>(idx), f[i],
-                                     f[i + 1], pair_bits<decltype(P)::value + 1>(rnd));
-    });
-    if constexpr (CHECK) {
-        const int64_t plane = kp.plane;
-        R du2 = R(0), u2 = R(0);
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            acc[kStatUx + d] = ur[d];
-            du2 += (ur[d] - up[d]) * (ur[d] - up[d]);
-            u2 += ur[d] * ur[d];
-            usnap[(int64_t)d * plane + idx] = ur[d];
-        }
-        acc[kStatDu2] = du2;
-        acc[kStatU2] = u2;
-        acc[kStatDrho] = drho;
-        acc[kStatNonFinite] = isfinite(drho) ? R(0) : R(1);
-    }
+    store_cell<L, S>(dst, idx, f, rnd);
+    if constexpr (CHECK) check_stats(ur, up, drho, usnap, kp.plane, idx, acc);
 }
 
-// Copy-through: the solid cells of a warp that holds fluid cells run
+// Copy-through: the solid cells that share an aligned group of 8 consecutive
+// cells (one 32-byte sector of a plane of 4-byte words) with a fluid cell run
 // cell_step with fluid = false, which stores their populations unchanged, so
-// the warp's stores fill whole sectors (plain and check steps).  For the PR
+// the stores fill whole sectors (plain and check steps).  Groups without fluid
+// cells are neither read nor written.  (The earlier rule, every solid cell of
+// a warp that holds fluid cells, also moved the all-solid sectors of mixed
+// warps: on a porous box of porosity 0.7 with grains of radius 6-10 it
+// touched 1.43x the fluid cells' bytes, the 8-cell groups 1.27x.)  For the PR
 // step of the 16-bit forms it is a per-solver choice (COPY), because there
 // its path costs registers: on the D3Q27 duct, which has no warp mixing
 // solid and fluid cells, it spills and the step is 6 % slower, while on a
@@ -879,6 +910,17 @@ __device__ __forceinline__ void cell_step(const KParams& kp, const Coef<typename
 // the other: 40 % slower on the porous box in FP32.)
 template <int MODEL, class S> __host__ __device__ constexpr bool copy_is_choice() {
     return MODEL != LBM_MODEL_IR && sizeof(S) == 2;
+}
+
+// Whether the aligned group of kCopyGroup cells holding cell idx has a fluid
+// cell among the warp's active lanes.  Lane l holds cell idx - (threadIdx.x &
+// 31) + l; cells of the group outside the warp count as solid (possible only
+// when a launch does not start on a group boundary, a step taken in parts).
+constexpr int kCopyGroup = 8;
+__device__ __forceinline__ bool group_has_fluid(bool fluid, int idx) {
+    const uint32_t b = __ballot_sync(__activemask(), fluid);
+    const int first = (int)(threadIdx.x & 31) - (idx & (kCopyGroup - 1));   // -7 .. 31
+    return ((((uint64_t)b << 32) >> (first + 32)) & ((1u << kCopyGroup) - 1u)) != 0;
 }
 
 // BLOCK: threads per block, chosen per (lattice, model, storage, size class)
@@ -913,9 +955,9 @@ k_step(const KArgs a, const SrcPlanes<S> src, const DstPlanes<S> dst,
     R acc[kNumStats];
     if constexpr (!CHECK) {
         if constexpr (COPY) {
-            // a warp without fluid cells has nothing to do; in any other warp
+            // a group without fluid cells has nothing to do; in any other group
             // the solid cells inside the domain copy their populations through
-            if (!__any_sync(__activemask(), active) || !inside) return;
+            if (!group_has_fluid(active, idx) || !inside) return;
             cell_step<L, MODEL, S, false>(kp, coef<R>(a), src, dst, lk, idx, tau, usnap, rnd, acc,
                                           active);
         } else {
@@ -927,8 +969,7 @@ k_step(const KArgs a, const SrcPlanes<S> src, const DstPlanes<S> dst,
         for (int k = 0; k < kNumStats; ++k) acc[k] = R(0);
         if constexpr (COPY) {
             // solid cells add nothing to the sums: their velocity and snapshot are 0
-            const bool warp_fluid = __any_sync(__activemask(), active);
-            if (warp_fluid && inside)
+            if (group_has_fluid(active, idx) && inside)
                 cell_step<L, MODEL, S, true>(kp, coef<R>(a), src, dst, lk, idx, tau, usnap, rnd, acc,
                                              active);
         } else {
@@ -1021,6 +1062,204 @@ k_step2(const KArgs a, const SrcPlanes<S> src, const DstPlanes<S> dst,
 }
 
 // ---------------------------------------------------------------------------
+// Compact layout (LBM_FLAG_COMPACT).  The population planes, the link words,
+// tau and the check-step snapshot hold the stepped fluid cells only: slot k is
+// the k-th fluid cell in cell-index order, cellidx[k] its cell index, and
+// rank[n] the slot of cell n (-1 for a solid cell).  One thread per slot, so
+// every lane of a warp is a fluid cell and every store fills whole sectors,
+// whereas on a porous medium the dense layout also moves the solid cells that
+// share a DRAM access with fluid ones.  The pull reads population i of the
+// cell at x - c_i from slot rank[x - c_i] (a solid source: the cell's own
+// opposite population, as in the dense layout); the rank words a warp reads
+// lie in a few rows and mostly come from L1.  Per cell the arithmetic is the
+// dense step's (the same collision code, the same stochastic-rounding hash of
+// the cell index); compiled into another kernel, it may differ from it by the
+// compiler's multiply-add contraction, i.e. to round-off.
+template <class L, class S, class Src>
+__device__ __forceinline__ void gather_compact(const KParams& kp, const Src& P, uint32_t lk,
+                                               int idx, int slot, const int* __restrict__ rank,
+                                               typename Store<S>::R (&v)[L::Q]) {
+    const PullOffsets o = pull_offsets(kp, idx);
+    v[0] = Store<S>::template ld<L, 0>(P.template at<0>(slot));
+    if (__all_sync(__activemask(), lk == 0u)) {
+        static_for<1, L::Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            const int k = __ldg(rank + idx + o.template of<L, i>());
+            v[i] = Store<S>::template ld<L, i>(P.template at<i>(k));
+        });
+    } else {
+        static_for<1, L::Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            const S* p;
+            if ((lk >> i) & 1u)
+                p = P.template at<L::opp(i)>(slot);
+            else
+                p = P.template at<i>(__ldg(rank + idx + o.template of<L, i>()));
+            v[i] = Store<S>::template ld<L, i>(p);   // opposite planes share w_i
+        });
+    }
+}
+
+// One fluid cell of one time step in the compact layout (as cell_step).
+template <class L, int MODEL, class S, bool CHECK, class Src, class Dst>
+__device__ __forceinline__ void compact_cell(const KParams& kp, const Coef<typename Store<S>::R>& c,
+                                             const Src& src, const Dst& dst, uint32_t lk, int idx,
+                                             int slot, const int* __restrict__ rank,
+                                             typename Store<S>::R* __restrict__ tau,
+                                             typename Store<S>::R* __restrict__ usnap, uint32_t rnd,
+                                             typename Store<S>::R (&acc)[kNumStats]) {
+    using R = typename Store<S>::R;
+    R up[3] = {R(0), R(0), R(0)};
+    if constexpr (CHECK) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) up[d] = usnap[(int64_t)d * kp.plane + slot];
+    }
+    R f[L::Q];
+    gather_compact<L, S>(kp, src, lk, idx, slot, rank, f);
+    R drho, ur[3];
+    if constexpr (MODEL != LBM_MODEL_IR) {
+        R t = tau[slot];
+        collide_pr<L, S, MODEL == kModelPRImplicit>(c, kp.flags, f, t, drho, ur);
+        tau[slot] = t;
+    } else {
+        collide_ir<L, S>(c, kp.flags, f, drho, ur);
+    }
+    store_cell<L, S>(dst, slot, f, rnd);
+    if constexpr (CHECK) check_stats(ur, up, drho, usnap, kp.plane, slot, acc);
+}
+
+// Register budget of the compact step: the dense step's (BLBM_COMPACT_MINB
+// overrides it at build time for the FP32-arithmetic forms).
+#ifndef BLBM_COMPACT_MINB
+#define BLBM_COMPACT_MINB -1
+#endif
+template <class L, int MODEL, class S, bool CHECK> constexpr int compact_min_blocks() {
+    if (std::is_same<typename Store<S>::R, double>::value) return 0;
+    if (BLBM_COMPACT_MINB >= 0) return BLBM_COMPACT_MINB;
+    // IR: 6 blocks of 256 (40 registers, no spill): on the 256^3 porous box
+    // 378 -> 361 us (FP32) and 318 -> 302 us (FP16) against the allocator's
+    // 38 registers; PR keeps the dense step's budget (6 blocks spilled and
+    // made the FP16 step 7 % slower)
+    if (MODEL == LBM_MODEL_IR && !CHECK) return 6;
+    return step_min_blocks<L, MODEL, S, CHECK, kBlock>();
+}
+
+template <class L, int MODEL, class S, bool CHECK>
+__global__ void __launch_bounds__(kBlock, compact_min_blocks<L, MODEL, S, CHECK>())
+k_step_compact(const KArgs a, const SrcPlanes<S> src, const DstPlanes<S> dst,
+               const uint32_t* __restrict__ links, const int* __restrict__ cellidx,
+               const int* __restrict__ rank, typename Store<S>::R* __restrict__ tau,
+               typename Store<S>::R* __restrict__ usnap, double* __restrict__ partials,
+               uint32_t* __restrict__ rng_ctr, int parity) {
+    using R = typename Store<S>::R;
+    const KParams& kp = a.kp;
+    const int slot = blockIdx.x * kBlock + threadIdx.x;
+    uint32_t seed = 0u;
+    if constexpr (Store<S>::kStochastic) {
+        // this launch reads counter[parity] and leaves counter + 1 for the next
+        seed = __ldg(rng_ctr + parity);
+        if (blockIdx.x == 0 && threadIdx.x == 0) rng_ctr[parity ^ 1] = seed + 1u;
+    }
+    R acc[kNumStats];
+    if constexpr (CHECK) {
+#pragma unroll
+        for (int k = 0; k < kNumStats; ++k) acc[k] = R(0);
+    }
+    if (slot < kp.nslots) {
+        const int idx = __ldg(cellidx + slot);
+        const uint32_t lk = __ldg(links + slot);
+        uint32_t rnd = 0u;
+        if constexpr (Store<S>::kStochastic)
+            rnd = pcg_hash(((uint32_t)idx + kp.hash_offset) ^ (seed * 0x9e3779b9u));
+        compact_cell<L, MODEL, S, CHECK>(kp, coef<R>(a), src, dst, lk, idx, slot, rank, tau, usnap,
+                                         rnd, acc);
+    }
+    if constexpr (CHECK) block_sum_store(acc, partials + (int64_t)blockIdx.x * kNumStats);
+}
+
+// Plain compact step over a persistent grid: each thread walks the slots
+// slot, slot + stride, ... and loads the next slot's cell index and link word
+// before it steps the current one, so of the three dependent loads of a slot
+// (cell index, neighbour slots, populations) only the last two are on the
+// critical path.  It pays for the IR step of the 16-bit forms (256^3 porous
+// box, D3Q19 FP16: 306 -> 268 us).  The FP32 forms need more registers for it
+// than their budgets hold: IR spilled at 6 blocks per SM (417 us) and ran at
+// 391 us with 5, against 364 us for the one-slot kernel; PR gained nothing.
+template <int MODEL, class S> constexpr bool compact_loop() {
+    return MODEL == LBM_MODEL_IR && sizeof(S) == 2;
+}
+// (BLBM_COMPACT_LOOP_MINB overrides its register budget at build time.)
+#ifndef BLBM_COMPACT_LOOP_MINB
+#define BLBM_COMPACT_LOOP_MINB -1
+#endif
+template <class L, int MODEL, class S> constexpr int compact_loop_min_blocks() {
+    if (BLBM_COMPACT_LOOP_MINB >= 0) return BLBM_COMPACT_LOOP_MINB;
+    return compact_min_blocks<L, MODEL, S, false>();
+}
+
+template <class L, int MODEL, class S>
+__global__ void __launch_bounds__(kBlock, compact_loop_min_blocks<L, MODEL, S>())
+k_step_compact_loop(const KArgs a, const SrcPlanes<S> src, const DstPlanes<S> dst,
+                    const uint32_t* __restrict__ links, const int* __restrict__ cellidx,
+                    const int* __restrict__ rank, typename Store<S>::R* __restrict__ tau,
+                    uint32_t* __restrict__ rng_ctr, int parity) {
+    using R = typename Store<S>::R;
+    const KParams& kp = a.kp;
+    const int n = kp.nslots, stride = gridDim.x * kBlock;
+    uint32_t seed = 0u;
+    if constexpr (Store<S>::kStochastic) {
+        // this launch reads counter[parity] and leaves counter + 1 for the next
+        seed = __ldg(rng_ctr + parity);
+        if (blockIdx.x == 0 && threadIdx.x == 0) rng_ctr[parity ^ 1] = seed + 1u;
+    }
+    int slot = blockIdx.x * kBlock + threadIdx.x;
+    int idx = 0;
+    uint32_t lk = 0u;
+    if (slot < n) {
+        idx = __ldg(cellidx + slot);
+        lk = __ldg(links + slot);
+    }
+    R acc[kNumStats];
+    for (; slot < n; slot += stride) {
+        const int next = slot + stride;
+        int nidx = 0;
+        uint32_t nlk = 0u;
+        if (next < n) {
+            nidx = __ldg(cellidx + next);
+            nlk = __ldg(links + next);
+        }
+        uint32_t rnd = 0u;
+        if constexpr (Store<S>::kStochastic)
+            rnd = pcg_hash(((uint32_t)idx + kp.hash_offset) ^ (seed * 0x9e3779b9u));
+        compact_cell<L, MODEL, S, false>(kp, coef<R>(a), src, dst, lk, idx, slot, rank, tau,
+                                         nullptr, rnd, acc);
+        idx = nidx;
+        lk = nlk;
+    }
+}
+
+// link words of the compact layout: slot k gets the bits of cell cellidx[k]
+template <class L>
+__global__ void __launch_bounds__(kBlock)
+k_links_compact(const KParams kp, const uint8_t* __restrict__ mask,
+                const int* __restrict__ cellidx, uint32_t* __restrict__ links) {
+    const int slot = blockIdx.x * kBlock + threadIdx.x;
+    if (slot >= kp.nslots) return;
+    const int nx = kp.nx, ny = kp.ny, nz = kp.nz;
+    int x, y, z;
+    cell_xyz(kp, cellidx[slot], x, y, z);
+    uint32_t bits = 0;
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+        const int xs = (x - L::cx(i) + nx) % nx;
+        const int ys = (y - L::cy(i) + ny) % ny;
+        const int zs = (z - L::cz(i) + nz) % nz;
+        if (mask[xs + nx * (ys + ny * zs)]) bits |= 1u << i;
+    }
+    links[slot] = bits;
+}
+
+// ---------------------------------------------------------------------------
 // Batched step: all resident domains of one (lattice, model, storage) in one
 // launch.  Block b works on domain block_dom[b]; each domain's blocks are
 // contiguous from desc.block_begin.  The current buffer of a domain is
@@ -1048,7 +1287,7 @@ template <> __device__ __forceinline__ const Coef<double>& bcoef<double>(const B
 
 // One check step of one tile (kBlock consecutive cells of one domain): as
 // k_step's check step, with the copy-through for every form (the solid cells
-// of a warp with fluid cells copy their populations through).
+// of a group with fluid cells copy their populations through).
 template <class L, int MODEL, class S>
 __device__ __forceinline__ void batch_tile_check(const BatchDesc& D, int tile, int phase,
                                                  double* __restrict__ partials) {
@@ -1069,11 +1308,11 @@ __device__ __forceinline__ void batch_tile_check(const BatchDesc& D, int tile, i
     }
     const uint32_t lk = inside ? __ldg(D.links + idx) : kSolidBit;
     const bool active = !(lk & kSolidBit);
-    const bool warp_fluid = __any_sync(__activemask(), active);
+    const bool group_fluid = group_has_fluid(active, idx);
     R acc[kNumStats];
 #pragma unroll
     for (int k = 0; k < kNumStats; ++k) acc[k] = R(0);
-    if (warp_fluid && inside)
+    if (group_fluid && inside)
         cell_step<L, MODEL, S, true>(kp, bcoef<R>(D), src, dst, lk, idx, (R*)D.tau, (R*)D.usnap,
                                      rnd, acc, active);
     block_sum_store(acc, partials + (int64_t)tile * kNumStats);
@@ -1105,9 +1344,9 @@ __device__ __forceinline__ void batch_tile_plain(const BatchDesc& D, int tile, i
         if constexpr (Store<S>::kStochastic) rnd = pcg_hash(((uint32_t)idx + kp.hash_offset) ^ (seed * 0x9e3779b9u));
         const uint32_t lk = inside ? __ldg(D.links + idx) : kSolidBit;
         const bool active = !(lk & kSolidBit);
-        const bool warp_fluid = __any_sync(__activemask(), active);
+        const bool group_fluid = group_has_fluid(active, idx);
         R acc[kNumStats];
-        if (warp_fluid && inside)
+        if (group_fluid && inside)
             cell_step<L, MODEL, S, false>(kp, bcoef<R>(D), src, dst, lk, idx, (R*)D.tau,
                                           (R*)D.usnap, rnd, acc, active);
     }
@@ -1162,7 +1401,22 @@ k_step_batch(const BatchDesc* __restrict__ descs, const int* __restrict__ tile_d
         batch_tile_plain<L, MODEL, S, T, C>(descs[tile_dom[t]], t, phase);
 }
 
-// macroscopic fields of the streamed populations
+// density and velocity u = (j + F/2) / rho of gathered populations
+template <class L, class S>
+__device__ __forceinline__ void fields_of(const KArgs& a, const typename Store<S>::R (&v)[L::Q],
+                                          double& r, double (&u)[3]) {
+    using R = typename Store<S>::R;
+    const Mom<R> m = moments<L, S>(v);
+    const Coef<R>& c = coef<R>(a);
+    const R rr = R(1) + m.d;
+    const R inv = R(1) / rr;
+    r = (double)rr;
+    u[0] = (double)((m.jx + R(0.5) * rr * c.g[0]) * inv);
+    u[1] = (double)((m.jy + R(0.5) * rr * c.g[1]) * inv);
+    if constexpr (L::D == 3) u[2] = (double)((m.jz + R(0.5) * rr * c.g[2]) * inv);
+}
+
+// macroscopic fields of the streamed populations (solid cells: 0)
 template <class L, class S>
 __global__ void __launch_bounds__(kBlock)
 k_fields(const KArgs a, const SrcPlanes<S> f, const uint32_t* __restrict__ links,
@@ -1177,14 +1431,7 @@ k_fields(const KArgs a, const SrcPlanes<S> f, const uint32_t* __restrict__ links
     if (!(lk & kSolidBit)) {
         R v[L::Q];
         gather<L, S>(kp, f, lk, idx, v);
-        const Mom<R> m = moments<L, S>(v);
-        const Coef<R>& c = coef<R>(a);
-        const R rr = R(1) + m.d;
-        const R inv = R(1) / rr;
-        r = (double)rr;
-        u[0] = (double)((m.jx + R(0.5) * rr * c.g[0]) * inv);
-        u[1] = (double)((m.jy + R(0.5) * rr * c.g[1]) * inv);
-        if constexpr (L::D == 3) u[2] = (double)((m.jz + R(0.5) * rr * c.g[2]) * inv);
+        fields_of<L, S>(a, v, r, u);
     }
     if (rho) rho[idx] = r;
     if (ux) ux[idx] = u[0];
@@ -1192,10 +1439,35 @@ k_fields(const KArgs a, const SrcPlanes<S> f, const uint32_t* __restrict__ links
     if (uz) uz[idx] = u[2];
 }
 
-// grid-stride reductions: flow sums of u_real (gathered) or state totals
-template <class L, class S, int MODE>
+// the same from the compact layout, one thread per cell of the box
+template <class L, class S>
+__global__ void __launch_bounds__(kBlock)
+k_fields_compact(const KArgs a, const SrcPlanes<S> f, const uint32_t* __restrict__ links,
+                 const int* __restrict__ rank, double* __restrict__ rho, double* __restrict__ ux,
+                 double* __restrict__ uy, double* __restrict__ uz) {
+    using R = typename Store<S>::R;
+    const KParams& kp = a.kp;
+    const int idx = blockIdx.x * kBlock + threadIdx.x;
+    if (idx >= kp.ncells) return;
+    const int slot = rank[idx];
+    double r = 0.0, u[3] = {0.0, 0.0, 0.0};
+    if (slot >= 0) {
+        R v[L::Q];
+        gather_compact<L, S>(kp, f, links[slot], idx, slot, rank, v);
+        fields_of<L, S>(a, v, r, u);
+    }
+    if (rho) rho[idx] = r;
+    if (ux) ux[idx] = u[0];
+    if (uy) uy[idx] = u[1];
+    if (uz) uz[idx] = u[2];
+}
+
+// grid-stride reductions: flow sums of u_real (gathered) or state totals,
+// over the cells of the box (dense layout) or the slots (COMPACT)
+template <class L, class S, int MODE, bool COMPACT>
 __global__ void __launch_bounds__(kBlock)
 k_reduce(const KArgs a, const SrcPlanes<S> f, const uint32_t* __restrict__ links,
+         const int* __restrict__ cellidx, const int* __restrict__ rank,
          double* __restrict__ partials) {
     using R = typename Store<S>::R;
     const KParams& kp = a.kp;
@@ -1203,16 +1475,20 @@ k_reduce(const KArgs a, const SrcPlanes<S> f, const uint32_t* __restrict__ links
 #pragma unroll
     for (int k = 0; k < kNumStats; ++k) acc[k] = 0.0;
     const int stride = gridDim.x * kBlock;
-    for (int idx = blockIdx.x * kBlock + threadIdx.x; idx < kp.ncells; idx += stride) {
-        const uint32_t lk = links[idx];
-        if (lk & kSolidBit) continue;
+    const int n_end = COMPACT ? kp.nslots : kp.ncells;
+    for (int n = blockIdx.x * kBlock + threadIdx.x; n < n_end; n += stride) {
+        const uint32_t lk = links[n];
+        if (!COMPACT && (lk & kSolidBit)) continue;
         R v[L::Q];
         if constexpr (MODE == kReduceFlow) {
-            gather<L, S>(kp, f, lk, idx, v);
+            if constexpr (COMPACT)
+                gather_compact<L, S>(kp, f, lk, cellidx[n], n, rank, v);
+            else
+                gather<L, S>(kp, f, lk, n, v);
         } else {
             static_for<0, L::Q>([&](auto I) {
                 constexpr int i = decltype(I)::value;
-                v[i] = Store<S>::template ld<L, i>(f.p[i] + idx);
+                v[i] = Store<S>::template ld<L, i>(f.template at<i>(n));
             });
         }
         const Mom<R> m = moments<L, S>(v);
@@ -1262,17 +1538,25 @@ k_links(const KParams kp, const uint8_t* __restrict__ mask, uint32_t* __restrict
     links[idx] = bits;
 }
 
-// FP64 full populations <-> stored offsets, one population plane at a time
+// FP64 full populations <-> stored offsets, one population plane at a time.
+// Compact layout (rank != nullptr): the fluid cells' values move through
+// their slots; solid cells are not stored and read back as the rest state w_q.
 template <class L, class S>
 __global__ void __launch_bounds__(kBlock)
-k_convert(const KParams kp, int q, bool to_device, S* __restrict__ f, double* __restrict__ buf) {
+k_convert(const KParams kp, int q, bool to_device, S* __restrict__ f, double* __restrict__ buf,
+          const int* __restrict__ rank) {
     const int idx = blockIdx.x * kBlock + threadIdx.x;
     if (idx >= kp.ncells) return;
     double w = 0.0;
 #pragma unroll
     for (int i = 0; i < L::Q; ++i)
         if (i == q) w = L::w(i);
-    S* p = f + pop_base<S>(q, kp.plane) + (int64_t)pop_step<S>(q) * idx;
+    const int n = rank ? rank[idx] : idx;
+    if (n < 0) {
+        if (!to_device) buf[idx] = w;
+        return;
+    }
+    S* p = f + pop_base<S>(q, kp.plane) + (int64_t)pop_step<S>(q) * n;
     if (to_device)
         *p = Store<S>::enc(buf[idx] - w, w);
     else
@@ -1319,17 +1603,19 @@ k_halo(const KParams kp, S* __restrict__ f, S* __restrict__ buf, int side, bool 
 }
 
 // full FP64 populations of listed cells: out[i * n + k] = f_i(cells[k])
+// (compact layout: a solid cell reads as the rest state w_i)
 template <class L, class S>
 __global__ void __launch_bounds__(kBlock)
 k_gather_cells(const KParams kp, const S* __restrict__ f, const int64_t* __restrict__ cells,
-               int n, double* __restrict__ out) {
+               int n, double* __restrict__ out, const int* __restrict__ rank) {
     const int k = blockIdx.x * kBlock + threadIdx.x;
     if (k >= n) return;
-    const int64_t c = cells[k];
+    const int64_t c = rank ? (int64_t)rank[cells[k]] : cells[k];
     static_for<0, L::Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
         out[(int64_t)i * n + k] =
-            Store<S>::dec(f[pop_base<S>(i, kp.plane) + (int64_t)pop_step<S>(i) * c], L::w(i)) + L::w(i);
+            c < 0 ? L::w(i)
+                  : Store<S>::dec(f[pop_base<S>(i, kp.plane) + (int64_t)pop_step<S>(i) * c], L::w(i)) + L::w(i);
     });
 }
 
@@ -1446,10 +1732,48 @@ cudaError_t launch_step_c(bool check, const KParams& kp, const StepArgs& s, cuda
     return cudaGetLastError();
 }
 
-// The copy-through is on for every form but the PR step of the 16-bit ones,
-// which follows the solver's geometry (s.copy).
+template <class L, int MODEL, class S>
+cudaError_t launch_step_compact(bool check, const KParams& kp, const StepArgs& s, cudaStream_t st) {
+    using R = typename Store<S>::R;
+    const KArgs a = make_args<L>(kp);
+    const int grid = step_grid(kp.nslots);
+    const SrcPlanes<S> src = src_planes<L, S>(s.fsrc, kp.plane);
+    const DstPlanes<S> dst = dst_planes<L, S>(s.fdst, kp.plane);
+    if (check) {
+        k_step_compact<L, MODEL, S, true><<<grid, kBlock, 0, st>>>(
+            a, src, dst, s.links, s.cellidx, s.rank, (R*)s.tau, (R*)s.usnap, s.partials,
+            s.rng_ctr, s.parity);
+    } else if constexpr (compact_loop<MODEL, S>()) {
+        // persistent: as many blocks as are resident at once, at most one per 256 slots
+        static const int resident = [] {   // blocks per SM (per instantiation)
+            int r = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, k_step_compact_loop<L, MODEL, S>,
+                                                              kBlock, 0) != cudaSuccess) {
+                cudaGetLastError();
+                r = 1;
+            }
+            return r < 1 ? 1 : r;
+        }();
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int pgrid = std::min(grid, std::max(1, resident * sms));
+        k_step_compact_loop<L, MODEL, S><<<pgrid, kBlock, 0, st>>>(
+            a, src, dst, s.links, s.cellidx, s.rank, (R*)s.tau, s.rng_ctr, s.parity);
+    } else {
+        k_step_compact<L, MODEL, S, false><<<grid, kBlock, 0, st>>>(
+            a, src, dst, s.links, s.cellidx, s.rank, (R*)s.tau, (R*)s.usnap, s.partials,
+            s.rng_ctr, s.parity);
+    }
+    return cudaGetLastError();
+}
+
+// The compact layout has its own kernel.  In the dense one the copy-through
+// is on for every form but the PR step of the 16-bit ones, which follows the
+// solver's geometry (s.copy).
 template <class L, int MODEL, class S>
 cudaError_t launch_step_t(bool check, const KParams& kp, const StepArgs& s, cudaStream_t st) {
+    if (s.rank) return launch_step_compact<L, MODEL, S>(check, kp, s, st);
     if constexpr (copy_is_choice<MODEL, S>()) {
         if (!s.copy) return launch_step_c<L, MODEL, S, false>(check, kp, s, st);
     }
@@ -1533,68 +1857,82 @@ cudaError_t launch_batch_lat(int model, int storage, bool check, const BatchDesc
 
 template <class L>
 cudaError_t launch_links_lat(const KParams& kp, const uint8_t* mask, uint32_t* links,
-                             cudaStream_t st) {
-    k_links<L><<<step_grid(kp.ncells), kBlock, 0, st>>>(kp, mask, links);
+                             const int* cellidx, cudaStream_t st) {
+    if (cellidx)
+        k_links_compact<L><<<step_grid(kp.nslots), kBlock, 0, st>>>(kp, mask, cellidx, links);
+    else
+        k_links<L><<<step_grid(kp.ncells), kBlock, 0, st>>>(kp, mask, links);
+    return cudaGetLastError();
+}
+
+template <class L, class S>
+cudaError_t launch_fields_s(const KArgs& a, const void* f, const uint32_t* links, const int* rank,
+                            double* rho, double* ux, double* uy, double* uz, cudaStream_t st) {
+    const int grid = step_grid(a.kp.ncells);
+    const SrcPlanes<S> P = src_planes<L, S>(f, a.kp.plane);
+    if (rank)
+        k_fields_compact<L, S><<<grid, kBlock, 0, st>>>(a, P, links, rank, rho, ux, uy, uz);
+    else
+        k_fields<L, S><<<grid, kBlock, 0, st>>>(a, P, links, rho, ux, uy, uz);
     return cudaGetLastError();
 }
 
 template <class L>
 cudaError_t launch_fields_lat(int storage, const KParams& kp, const void* f, const uint32_t* links,
-                              double* rho, double* ux, double* uy, double* uz, cudaStream_t st) {
+                              const int* rank, double* rho, double* ux, double* uy, double* uz,
+                              cudaStream_t st) {
     const KArgs a = make_args<L>(kp);
-    const int grid = step_grid(kp.ncells);
     switch (storage) {
-    case LBM_F32:
-        k_fields<L, float><<<grid, kBlock, 0, st>>>(a, src_planes<L, float>(f, kp.plane), links, rho, ux, uy, uz);
-        break;
-    case LBM_F64:
-        k_fields<L, double><<<grid, kBlock, 0, st>>>(a, src_planes<L, double>(f, kp.plane), links, rho, ux, uy, uz);
-        break;
-    case LBM_F16_OFS:
-        k_fields<L, __half><<<grid, kBlock, 0, st>>>(a, src_planes<L, __half>(f, kp.plane), links, rho, ux, uy, uz);
-        break;
-    case LBM_BF16_OFS:
-        k_fields<L, __nv_bfloat16><<<grid, kBlock, 0, st>>>(a, src_planes<L, __nv_bfloat16>(f, kp.plane), links, rho, ux, uy, uz);
-        break;
+    case LBM_F32: return launch_fields_s<L, float>(a, f, links, rank, rho, ux, uy, uz, st);
+    case LBM_F64: return launch_fields_s<L, double>(a, f, links, rank, rho, ux, uy, uz, st);
+    case LBM_F16_OFS: return launch_fields_s<L, __half>(a, f, links, rank, rho, ux, uy, uz, st);
+    case LBM_BF16_OFS: return launch_fields_s<L, __nv_bfloat16>(a, f, links, rank, rho, ux, uy, uz, st);
     default: return cudaErrorNotSupported;
     }
-    return cudaGetLastError();
 }
 
 template <class L, class S>
 cudaError_t launch_reduce_s(int mode, const KArgs& a, const void* f, const uint32_t* links,
-                            double* partials, int nblocks, cudaStream_t st) {
+                            const int* cellidx, const int* rank, double* partials, int nblocks,
+                            cudaStream_t st) {
     const SrcPlanes<S> P = src_planes<L, S>(f, a.kp.plane);
-    if (mode == kReduceFlow)
-        k_reduce<L, S, kReduceFlow><<<nblocks, kBlock, 0, st>>>(a, P, links, partials);
-    else
-        k_reduce<L, S, kReduceTotals><<<nblocks, kBlock, 0, st>>>(a, P, links, partials);
+    if (cellidx) {
+        if (mode == kReduceFlow)
+            k_reduce<L, S, kReduceFlow, true><<<nblocks, kBlock, 0, st>>>(a, P, links, cellidx, rank, partials);
+        else
+            k_reduce<L, S, kReduceTotals, true><<<nblocks, kBlock, 0, st>>>(a, P, links, cellidx, rank, partials);
+    } else {
+        if (mode == kReduceFlow)
+            k_reduce<L, S, kReduceFlow, false><<<nblocks, kBlock, 0, st>>>(a, P, links, nullptr, nullptr, partials);
+        else
+            k_reduce<L, S, kReduceTotals, false><<<nblocks, kBlock, 0, st>>>(a, P, links, nullptr, nullptr, partials);
+    }
     return cudaGetLastError();
 }
 
 template <class L>
 cudaError_t launch_reduce_lat(int storage, int mode, const KParams& kp, const void* f,
-                              const uint32_t* links, double* partials, int nblocks,
-                              cudaStream_t st) {
+                              const uint32_t* links, const int* cellidx, const int* rank,
+                              double* partials, int nblocks, cudaStream_t st) {
     const KArgs a = make_args<L>(kp);
     switch (storage) {
-    case LBM_F32: return launch_reduce_s<L, float>(mode, a, f, links, partials, nblocks, st);
-    case LBM_F64: return launch_reduce_s<L, double>(mode, a, f, links, partials, nblocks, st);
-    case LBM_F16_OFS: return launch_reduce_s<L, __half>(mode, a, f, links, partials, nblocks, st);
-    case LBM_BF16_OFS: return launch_reduce_s<L, __nv_bfloat16>(mode, a, f, links, partials, nblocks, st);
+    case LBM_F32: return launch_reduce_s<L, float>(mode, a, f, links, cellidx, rank, partials, nblocks, st);
+    case LBM_F64: return launch_reduce_s<L, double>(mode, a, f, links, cellidx, rank, partials, nblocks, st);
+    case LBM_F16_OFS: return launch_reduce_s<L, __half>(mode, a, f, links, cellidx, rank, partials, nblocks, st);
+    case LBM_BF16_OFS: return launch_reduce_s<L, __nv_bfloat16>(mode, a, f, links, cellidx, rank, partials, nblocks, st);
     default: return cudaErrorNotSupported;
     }
 }
 
 template <class L>
 cudaError_t launch_convert_lat(int storage, bool to_device, const KParams& kp, int q, void* f,
-                               double* buf, cudaStream_t st) {
+                               double* buf, const int* rank, cudaStream_t st) {
     const int grid = step_grid(kp.ncells);
     switch (storage) {
-    case LBM_F32: k_convert<L, float><<<grid, kBlock, 0, st>>>(kp, q, to_device, (float*)f, buf); break;
-    case LBM_F64: k_convert<L, double><<<grid, kBlock, 0, st>>>(kp, q, to_device, (double*)f, buf); break;
-    case LBM_F16_OFS: k_convert<L, __half><<<grid, kBlock, 0, st>>>(kp, q, to_device, (__half*)f, buf); break;
-    case LBM_BF16_OFS: k_convert<L, __nv_bfloat16><<<grid, kBlock, 0, st>>>(kp, q, to_device, (__nv_bfloat16*)f, buf); break;
+    case LBM_F32: k_convert<L, float><<<grid, kBlock, 0, st>>>(kp, q, to_device, (float*)f, buf, rank); break;
+    case LBM_F64: k_convert<L, double><<<grid, kBlock, 0, st>>>(kp, q, to_device, (double*)f, buf, rank); break;
+    case LBM_F16_OFS: k_convert<L, __half><<<grid, kBlock, 0, st>>>(kp, q, to_device, (__half*)f, buf, rank); break;
+    case LBM_BF16_OFS: k_convert<L, __nv_bfloat16><<<grid, kBlock, 0, st>>>(kp, q, to_device, (__nv_bfloat16*)f, buf, rank); break;
     default: return cudaErrorNotSupported;
     }
     return cudaGetLastError();
@@ -1602,13 +1940,13 @@ cudaError_t launch_convert_lat(int storage, bool to_device, const KParams& kp, i
 
 template <class L>
 cudaError_t launch_gather_lat(int storage, const KParams& kp, const void* f, const int64_t* cells,
-                              int n, double* out, cudaStream_t st) {
+                              int n, double* out, const int* rank, cudaStream_t st) {
     const int grid = (n + kBlock - 1) / kBlock;
     switch (storage) {
-    case LBM_F32: k_gather_cells<L, float><<<grid, kBlock, 0, st>>>(kp, (const float*)f, cells, n, out); break;
-    case LBM_F64: k_gather_cells<L, double><<<grid, kBlock, 0, st>>>(kp, (const double*)f, cells, n, out); break;
-    case LBM_F16_OFS: k_gather_cells<L, __half><<<grid, kBlock, 0, st>>>(kp, (const __half*)f, cells, n, out); break;
-    case LBM_BF16_OFS: k_gather_cells<L, __nv_bfloat16><<<grid, kBlock, 0, st>>>(kp, (const __nv_bfloat16*)f, cells, n, out); break;
+    case LBM_F32: k_gather_cells<L, float><<<grid, kBlock, 0, st>>>(kp, (const float*)f, cells, n, out, rank); break;
+    case LBM_F64: k_gather_cells<L, double><<<grid, kBlock, 0, st>>>(kp, (const double*)f, cells, n, out, rank); break;
+    case LBM_F16_OFS: k_gather_cells<L, __half><<<grid, kBlock, 0, st>>>(kp, (const __half*)f, cells, n, out, rank); break;
+    case LBM_BF16_OFS: k_gather_cells<L, __nv_bfloat16><<<grid, kBlock, 0, st>>>(kp, (const __nv_bfloat16*)f, cells, n, out, rank); break;
     default: return cudaErrorNotSupported;
     }
     return cudaGetLastError();
@@ -1651,27 +1989,30 @@ template <class L> void lattice_table(int* c, double* w) {
         return launch_step_lat<L>(model, storage, check, kp, a, st);                            \
     }                                                                                           \
     cudaError_t launch_links_##L(const KParams& kp, const uint8_t* mask, uint32_t* links,      \
-                                 cudaStream_t st) {                                             \
-        return launch_links_lat<L>(kp, mask, links, st);                                        \
+                                 const int* cellidx, cudaStream_t st) {                         \
+        return launch_links_lat<L>(kp, mask, links, cellidx, st);                               \
     }                                                                                           \
     cudaError_t launch_fields_##L(int storage, const KParams& kp, const void* f,               \
-                                  const uint32_t* links, double* rho, double* ux, double* uy,  \
-                                  double* uz, cudaStream_t st) {                                \
-        return launch_fields_lat<L>(storage, kp, f, links, rho, ux, uy, uz, st);                \
+                                  const uint32_t* links, const int* rank, double* rho,         \
+                                  double* ux, double* uy, double* uz, cudaStream_t st) {        \
+        return launch_fields_lat<L>(storage, kp, f, links, rank, rho, ux, uy, uz, st);          \
     }                                                                                           \
     cudaError_t launch_reduce_##L(int storage, int mode, const KParams& kp, const void* f,     \
-                                  const uint32_t* links, double* partials, int nblocks,        \
-                                  cudaStream_t st) {                                            \
-        return launch_reduce_lat<L>(storage, mode, kp, f, links, partials, nblocks, st);        \
+                                  const uint32_t* links, const int* cellidx, const int* rank,  \
+                                  double* partials, int nblocks, cudaStream_t st) {             \
+        return launch_reduce_lat<L>(storage, mode, kp, f, links, cellidx, rank, partials,       \
+                                    nblocks, st);                                               \
     }                                                                                           \
     cudaError_t launch_convert_##L(int storage, bool to_device, const KParams& kp, int q,      \
-                                   void* f, double* plane_buf, cudaStream_t st) {               \
-        return launch_convert_lat<L>(storage, to_device, kp, q, f, plane_buf, st);              \
+                                   void* f, double* plane_buf, const int* rank,                 \
+                                   cudaStream_t st) {                                           \
+        return launch_convert_lat<L>(storage, to_device, kp, q, f, plane_buf, rank, st);        \
     }                                                                                           \
     void lattice_table_##L(int* c, double* w) { lattice_table<L>(c, w); }                       \
     cudaError_t launch_gather_##L(int storage, const KParams& kp, const void* f,               \
-                                  const int64_t* cells, int n, double* out, cudaStream_t st) {  \
-        return launch_gather_lat<L>(storage, kp, f, cells, n, out, st);                         \
+                                  const int64_t* cells, int n, double* out, const int* rank,   \
+                                  cudaStream_t st) {                                            \
+        return launch_gather_lat<L>(storage, kp, f, cells, n, out, rank, st);                   \
     }                                                                                           \
     cudaError_t launch_halo_##L(int storage, const KParams& kp, void* f, void* buf, int side,  \
                                 bool pack, cudaStream_t st) {                                   \

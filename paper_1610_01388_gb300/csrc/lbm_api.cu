@@ -5,6 +5,11 @@
 //   f[2]      population offsets f_i - w_i, SoA [Q][plane], A/B buffers
 //   links     per-cell bounce-back bits (bit i: cell at x - c_i is solid;
 //             bit 31: the cell itself is solid)
+// With LBM_FLAG_COMPACT, f, links, tau and usnap hold the fluid cells only
+// (one slot each, in cell-index order; plane >= the fluid count), and two
+// more regions map between slots and cells:
+//   cellidx   cell index of each slot
+//   rank      slot of each cell, -1 for a solid cell
 //   tau       PR relaxation time per cell, updated in place
 //   usnap     check-step velocity snapshot [3][plane]
 //   partials  per-block FP64 reduction partials
@@ -71,10 +76,14 @@ bool storage_built(int storage) { return storage_bytes(storage) != 0; }
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
-Layout make_layout(int lat, int nx, int ny, int nz, const lbm_params& p) {
+// held: the cells the planes hold (every cell; the fluid cells in the
+// compact layout)
+Layout make_layout(int lat, int nx, int ny, int nz, const lbm_params& p, int64_t held) {
     Layout L{};
     const int64_t ncells = (int64_t)nx * ny * nz;
-    L.plane = (ncells + 63) / 64 * 64;
+    const bool compact = (p.flags & LBM_FLAG_COMPACT) != 0;
+    if (!compact) held = ncells;
+    L.plane = (held + 63) / 64 * 64;
     const int Q = lattice_q(lat);
     const size_t fb = align256((size_t)Q * L.plane * storage_bytes(p.storage));
     const size_t rs = arith_bytes(p.storage);
@@ -84,14 +93,19 @@ Layout make_layout(int lat, int nx, int ny, int nz, const lbm_params& p) {
     L.off_links = o; o += align256((size_t)L.plane * 4);
     L.off_tau = o; o += (p.model == LBM_MODEL_PR) ? align256((size_t)L.plane * rs) : 0;
     L.off_usnap = o; o += (p.check_every > 0) ? align256((size_t)3 * L.plane * rs) : 0;
-    const int g1 = step_grid((int)ncells), g2 = reduce_grid((int)ncells);
+    const int g1 = step_grid((int)held), g2 = reduce_grid((int)held);
     L.nparts = g1 > g2 ? g1 : g2;
     L.off_partials = o; o += align256((size_t)L.nparts * kNumStats * sizeof(double));
     L.off_stats = o; o += align256(2 * kNumStats * sizeof(double));
     L.off_mask = o; o += align256((size_t)ncells);
+    L.off_cellidx = o; o += compact ? align256((size_t)L.plane * 4) : 0;
+    L.off_rank = o; o += compact ? align256((size_t)ncells * 4) : 0;
     L.total = o;
     return L;
 }
+
+// cells the step kernels update: all of them (dense) or the slots (compact)
+int held_cells(const lbm_solver* s) { return s->rank ? s->kp.nslots : s->ncells; }
 
 lbm_status validate(int lat, int nx, int ny, int nz, const uint8_t* mask, const lbm_params* p) {
     if (!p) return fail(LBM_EINVAL, "params is NULL");
@@ -114,10 +128,12 @@ lbm_status validate(int lat, int nx, int ny, int nz, const uint8_t* mask, const 
         if (!std::isfinite(p->g[d])) return fail(LBM_EINVAL, "g must be finite");
     if (lat == LBM_D2Q9 && p->g[2] != 0.0) return fail(LBM_EINVAL, "D2Q9 needs g[2] == 0");
     if (p->check_every < 0) return fail(LBM_EINVAL, "check_every must be >= 0");
-    if (p->flags & ~(LBM_FLAG_BURNETT_X | LBM_FLAG_Z_GHOSTS))
+    if (p->flags & ~(LBM_FLAG_BURNETT_X | LBM_FLAG_Z_GHOSTS | LBM_FLAG_COMPACT))
         return fail(LBM_EINVAL, "unknown flags 0x%x", p->flags);
     if ((p->flags & LBM_FLAG_Z_GHOSTS) && (lat == LBM_D2Q9 || nz < 3))
         return fail(LBM_EINVAL, "ghost planes need a 3D lattice and nz >= 3 (got nz = %d)", nz);
+    if ((p->flags & LBM_FLAG_Z_GHOSTS) && (p->flags & LBM_FLAG_COMPACT))
+        return fail(LBM_EINVAL, "ghost planes need the dense layout (LBM_FLAG_COMPACT set)");
     if (p->newton_iters < 0 || p->newton_iters > 64)
         return fail(LBM_EINVAL, "newton_iters must be in 0..64 (got %d)", p->newton_iters);
     if (p->reserved != 0) return fail(LBM_EINVAL, "reserved must be 0");
@@ -178,6 +194,8 @@ cudaError_t launch_step(lbm_solver* s, bool check, cudaStream_t st) {
     a.block = s->block;
     a.cpt = s->cpt;
     a.copy = s->copy;
+    a.cellidx = s->cellidx;
+    a.rank = s->rank;
     const int km = kernel_model(s->p.model, s->kp.newton);
     switch (s->lat) {
     case LBM_D2Q9: return launch_step_D2Q9(km, s->p.storage, check, s->kp, a, st);
@@ -189,40 +207,40 @@ cudaError_t launch_step(lbm_solver* s, bool check, cudaStream_t st) {
 
 cudaError_t launch_links(lbm_solver* s, const uint8_t* mask) {
     switch (s->lat) {
-    case LBM_D2Q9: return launch_links_D2Q9(s->kp, mask, s->links, s->stream);
-    case LBM_D3Q15: return launch_links_D3Q15(s->kp, mask, s->links, s->stream);
-    case LBM_D3Q19: return launch_links_D3Q19(s->kp, mask, s->links, s->stream);
-    default: return launch_links_D3Q27(s->kp, mask, s->links, s->stream);
+    case LBM_D2Q9: return launch_links_D2Q9(s->kp, mask, s->links, s->cellidx, s->stream);
+    case LBM_D3Q15: return launch_links_D3Q15(s->kp, mask, s->links, s->cellidx, s->stream);
+    case LBM_D3Q19: return launch_links_D3Q19(s->kp, mask, s->links, s->cellidx, s->stream);
+    default: return launch_links_D3Q27(s->kp, mask, s->links, s->cellidx, s->stream);
     }
 }
 
 cudaError_t launch_fields(lbm_solver* s, double* rho, double* ux, double* uy, double* uz) {
     const void* f = s->f[s->cur];
     switch (s->lat) {
-    case LBM_D2Q9: return launch_fields_D2Q9(s->p.storage, s->kp, f, s->links, rho, ux, uy, uz, s->stream);
-    case LBM_D3Q15: return launch_fields_D3Q15(s->p.storage, s->kp, f, s->links, rho, ux, uy, uz, s->stream);
-    case LBM_D3Q19: return launch_fields_D3Q19(s->p.storage, s->kp, f, s->links, rho, ux, uy, uz, s->stream);
-    default: return launch_fields_D3Q27(s->p.storage, s->kp, f, s->links, rho, ux, uy, uz, s->stream);
+    case LBM_D2Q9: return launch_fields_D2Q9(s->p.storage, s->kp, f, s->links, s->rank, rho, ux, uy, uz, s->stream);
+    case LBM_D3Q15: return launch_fields_D3Q15(s->p.storage, s->kp, f, s->links, s->rank, rho, ux, uy, uz, s->stream);
+    case LBM_D3Q19: return launch_fields_D3Q19(s->p.storage, s->kp, f, s->links, s->rank, rho, ux, uy, uz, s->stream);
+    default: return launch_fields_D3Q27(s->p.storage, s->kp, f, s->links, s->rank, rho, ux, uy, uz, s->stream);
     }
 }
 
 cudaError_t launch_reduce(lbm_solver* s, int mode, int nblocks) {
     const void* f = s->f[s->cur];
     switch (s->lat) {
-    case LBM_D2Q9: return launch_reduce_D2Q9(s->p.storage, mode, s->kp, f, s->links, s->partials, nblocks, s->stream);
-    case LBM_D3Q15: return launch_reduce_D3Q15(s->p.storage, mode, s->kp, f, s->links, s->partials, nblocks, s->stream);
-    case LBM_D3Q19: return launch_reduce_D3Q19(s->p.storage, mode, s->kp, f, s->links, s->partials, nblocks, s->stream);
-    default: return launch_reduce_D3Q27(s->p.storage, mode, s->kp, f, s->links, s->partials, nblocks, s->stream);
+    case LBM_D2Q9: return launch_reduce_D2Q9(s->p.storage, mode, s->kp, f, s->links, s->cellidx, s->rank, s->partials, nblocks, s->stream);
+    case LBM_D3Q15: return launch_reduce_D3Q15(s->p.storage, mode, s->kp, f, s->links, s->cellidx, s->rank, s->partials, nblocks, s->stream);
+    case LBM_D3Q19: return launch_reduce_D3Q19(s->p.storage, mode, s->kp, f, s->links, s->cellidx, s->rank, s->partials, nblocks, s->stream);
+    default: return launch_reduce_D3Q27(s->p.storage, mode, s->kp, f, s->links, s->cellidx, s->rank, s->partials, nblocks, s->stream);
     }
 }
 
 cudaError_t launch_convert(lbm_solver* s, bool to_device, int q, double* buf, int which) {
     void* f = s->f[which];
     switch (s->lat) {
-    case LBM_D2Q9: return launch_convert_D2Q9(s->p.storage, to_device, s->kp, q, f, buf, s->stream);
-    case LBM_D3Q15: return launch_convert_D3Q15(s->p.storage, to_device, s->kp, q, f, buf, s->stream);
-    case LBM_D3Q19: return launch_convert_D3Q19(s->p.storage, to_device, s->kp, q, f, buf, s->stream);
-    default: return launch_convert_D3Q27(s->p.storage, to_device, s->kp, q, f, buf, s->stream);
+    case LBM_D2Q9: return launch_convert_D2Q9(s->p.storage, to_device, s->kp, q, f, buf, s->rank, s->stream);
+    case LBM_D3Q15: return launch_convert_D3Q15(s->p.storage, to_device, s->kp, q, f, buf, s->rank, s->stream);
+    case LBM_D3Q19: return launch_convert_D3Q19(s->p.storage, to_device, s->kp, q, f, buf, s->rank, s->stream);
+    default: return launch_convert_D3Q27(s->p.storage, to_device, s->kp, q, f, buf, s->rank, s->stream);
     }
 }
 
@@ -245,7 +263,7 @@ cudaError_t do_step(lbm_solver* s, bool check, cudaStream_t st) {
     s->cur ^= 1;
     s->steps += 1;
     if (check) {
-        e = launch_finalize(s->partials, step_grid(s->ncells), s->stats, st);
+        e = launch_finalize(s->partials, step_grid(held_cells(s)), s->stats, st);
         if (e != cudaSuccess) return e;
         e = cudaMemcpyAsync(s->host_stats, s->stats, kNumStats * sizeof(double),
                             cudaMemcpyDeviceToHost, st);
@@ -425,7 +443,27 @@ lbm_status lbm_workspace_bytes(lbm_lattice lat, int nx, int ny, int nz, const lb
     if (nx < 1 || ny < 1 || nz < 1) return fail(LBM_EINVAL, "extents must be >= 1");
     if ((int64_t)nx * ny * nz > (int64_t)0x7fffffff - 64) return fail(LBM_EINVAL, "too many cells");
     if (storage_bytes(p->storage) == 0) return fail(LBM_EINVAL, "unknown storage %d", p->storage);
-    *bytes = make_layout(lat, nx, ny, nz, *p).total;
+    // compact layout: sized as if every cell were fluid (an upper bound)
+    *bytes = make_layout(lat, nx, ny, nz, *p, (int64_t)nx * ny * nz).total;
+    return LBM_OK;
+}
+
+// fluid cells the step updates (ghost planes are not)
+static int64_t stepped_fluid(int nx, int ny, int nz, const uint8_t* mask, uint32_t flags) {
+    const int64_t nxy = (int64_t)nx * ny, n = nxy * nz;
+    const bool ghosts = (flags & LBM_FLAG_Z_GHOSTS) != 0;
+    int64_t nf = 0;
+    for (int64_t i = ghosts ? nxy : 0; i < (ghosts ? n - nxy : n); ++i) nf += mask[i] == 0;
+    return nf;
+}
+
+lbm_status lbm_workspace_bytes_for_mask(lbm_lattice lat, int nx, int ny, int nz,
+                                        const uint8_t* solid_mask, const lbm_params* p,
+                                        size_t* bytes) {
+    if (!bytes) return fail(LBM_EINVAL, "bytes is NULL");
+    lbm_status v = validate(lat, nx, ny, nz, solid_mask, p);
+    if (v != LBM_OK) return v;
+    *bytes = make_layout(lat, nx, ny, nz, *p, stepped_fluid(nx, ny, nz, solid_mask, p->flags)).total;
     return LBM_OK;
 }
 
@@ -450,8 +488,9 @@ static lbm_status create_impl(lbm_solver** out, lbm_lattice lat, int nx, int ny,
     // fluid cells: the stepped ones (ghost planes are not)
     const int nxy = nx * ny;
     const bool ghosts = (p->flags & LBM_FLAG_Z_GHOSTS) != 0;
+    const bool compact = (p->flags & LBM_FLAG_COMPACT) != 0;
     auto stepped = [&](int i) { return mask[i] == 0 && !(ghosts && (i < nxy || i >= s->ncells - nxy)); };
-    for (int i = 0; i < s->ncells; ++i) s->nfluid += stepped(i);
+    s->nfluid = stepped_fluid(nx, ny, nz, mask, p->flags);
     {
         // warps (32 consecutive cells) holding fluid cells, and those of them
         // that also hold solid cells: the copy-through choice of the 16-bit PR
@@ -466,7 +505,7 @@ static lbm_status create_impl(lbm_solver** out, lbm_lattice lat, int nx, int ny,
         }
         s->copy = 100 * mixed >= with_fluid ? 1 : 0;
     }
-    s->lay = make_layout(lat, nx, ny, nz, *p);
+    s->lay = make_layout(lat, nx, ny, nz, *p, s->nfluid);
     KParams& kp = s->kp;
     kp.nx = nx;
     kp.ny = ny;
@@ -474,6 +513,7 @@ static lbm_status create_impl(lbm_solver** out, lbm_lattice lat, int nx, int ny,
     kp.ncells = s->ncells;
     kp.cell_begin = 0;
     kp.cell_end = s->ncells;
+    kp.nslots = compact ? (int)s->nfluid : 0;
     kp.plane = s->lay.plane;
     kp.nu_p = p->mu_p;   // rho_0 = 1
     kp.sigma_y = p->sigma_y;
@@ -522,6 +562,18 @@ static lbm_status create_impl(lbm_solver** out, lbm_lattice lat, int nx, int ny,
     s->partials = (double*)(s->base + s->lay.off_partials);
     s->stats = (double*)(s->base + s->lay.off_stats);
     uint8_t* dmask = (uint8_t*)(s->base + s->lay.off_mask);
+    std::vector<int> h_cellidx, h_rank;
+    if (compact) {
+        s->cellidx = (int*)(s->base + s->lay.off_cellidx);
+        s->rank = (int*)(s->base + s->lay.off_rank);
+        h_cellidx.reserve((size_t)s->nfluid);
+        h_rank.assign((size_t)s->ncells, -1);
+        for (int i = 0; i < s->ncells; ++i)
+            if (stepped(i)) {
+                h_rank[i] = (int)h_cellidx.size();
+                h_cellidx.push_back(i);
+            }
+    }
 
     lbm_status rc = LBM_OK;
     do {
@@ -530,6 +582,10 @@ static lbm_status create_impl(lbm_solver** out, lbm_lattice lat, int nx, int ny,
         std::memset(s->host_stats, 0, kNumStats * sizeof(double));
         const size_t fb = (size_t)s->Q * s->lay.plane * storage_bytes(p->storage);
         if ((e = cudaMemcpyAsync(dmask, mask, (size_t)s->ncells, cudaMemcpyHostToDevice, s->stream)) != cudaSuccess) break;
+        if (compact) {
+            if ((e = cudaMemcpyAsync(s->cellidx, h_cellidx.data(), h_cellidx.size() * sizeof(int), cudaMemcpyHostToDevice, s->stream)) != cudaSuccess) break;
+            if ((e = cudaMemcpyAsync(s->rank, h_rank.data(), h_rank.size() * sizeof(int), cudaMemcpyHostToDevice, s->stream)) != cudaSuccess) break;
+        }
         if ((e = launch_links(s, dmask)) != cudaSuccess) break;
         if ((e = cudaMemsetAsync(s->f[0], 0, fb, s->stream)) != cudaSuccess) break;
         if ((e = cudaMemsetAsync(s->f[1], 0, fb, s->stream)) != cudaSuccess) break;
@@ -709,6 +765,7 @@ lbm_status lbm_step(lbm_solver* s, int64_t nsteps) {
 lbm_status lbm_step_cells(lbm_solver* s, int64_t cell_begin, int64_t cell_end) {
     lbm_status v = enter(s);
     if (v != LBM_OK) return v;
+    if (s->rank) return fail(LBM_EINVAL, "the compact layout takes whole steps only (lbm_step)");
     if (cell_begin < 0 || cell_end < cell_begin || cell_end > s->ncells)
         return fail(LBM_EINVAL, "cell range [%lld, %lld) is not within 0..%d", (long long)cell_begin,
                     (long long)cell_end, s->ncells);
@@ -731,6 +788,8 @@ lbm_status lbm_step_cells(lbm_solver* s, int64_t cell_begin, int64_t cell_end) {
     a.block = kBlock;
     a.cpt = 1;
     a.copy = s->copy;
+    a.cellidx = nullptr;
+    a.rank = nullptr;
     const int km = kernel_model(s->p.model, s->kp.newton);
     cudaError_t e;
     switch (s->lat) {
@@ -746,6 +805,7 @@ lbm_status lbm_step_cells(lbm_solver* s, int64_t cell_begin, int64_t cell_end) {
 lbm_status lbm_step_commit(lbm_solver* s) {
     lbm_status v = enter(s);
     if (v != LBM_OK) return v;
+    if (s->rank) return fail(LBM_EINVAL, "the compact layout takes whole steps only (lbm_step)");
     const int64_t k = s->p.check_every;
     if (k > 0 && (s->steps + 1) % k == 0)
         return fail(LBM_EINVAL, "the next step is a check step: take it whole with lbm_step");
@@ -785,7 +845,7 @@ lbm_status lbm_fields(lbm_solver* s, double* rho, double* ux, double* uy, double
 
 static lbm_status reduce_to_host(lbm_solver* s, int mode, double* out) {
     WAIT(s, "reduction");
-    const int nb = reduce_grid(s->ncells);
+    const int nb = reduce_grid(held_cells(s));
     CK(s, launch_reduce(s, mode, nb), "reduction kernel");
     CK(s, launch_finalize(s->partials, nb, s->stats + kNumStats, s->stream), "finalize kernel");
     CK(s, cudaMemcpyAsync(out, s->stats + kNumStats, kNumStats * sizeof(double), cudaMemcpyDeviceToHost, s->stream), "reduction copy");
@@ -884,10 +944,10 @@ lbm_status lbm_get_populations_cells(lbm_solver* s, const int64_t* cells, int64_
     if (e == cudaSuccess) {
         const void* fcur = s->f[s->cur];
         switch (s->lat) {
-        case LBM_D2Q9: e = launch_gather_D2Q9(s->p.storage, s->kp, fcur, d_cells, (int)n, d_out, s->stream); break;
-        case LBM_D3Q15: e = launch_gather_D3Q15(s->p.storage, s->kp, fcur, d_cells, (int)n, d_out, s->stream); break;
-        case LBM_D3Q19: e = launch_gather_D3Q19(s->p.storage, s->kp, fcur, d_cells, (int)n, d_out, s->stream); break;
-        default: e = launch_gather_D3Q27(s->p.storage, s->kp, fcur, d_cells, (int)n, d_out, s->stream); break;
+        case LBM_D2Q9: e = launch_gather_D2Q9(s->p.storage, s->kp, fcur, d_cells, (int)n, d_out, s->rank, s->stream); break;
+        case LBM_D3Q15: e = launch_gather_D3Q15(s->p.storage, s->kp, fcur, d_cells, (int)n, d_out, s->rank, s->stream); break;
+        case LBM_D3Q19: e = launch_gather_D3Q19(s->p.storage, s->kp, fcur, d_cells, (int)n, d_out, s->rank, s->stream); break;
+        default: e = launch_gather_D3Q27(s->p.storage, s->kp, fcur, d_cells, (int)n, d_out, s->rank, s->stream); break;
         }
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(f, d_out, out_bytes, cudaMemcpyDeviceToHost, s->stream);
@@ -898,18 +958,31 @@ lbm_status lbm_get_populations_cells(lbm_solver* s, const int64_t* cells, int64_
     return LBM_OK;
 }
 
+// The slots' cell indices (compact layout), for the tau transfers.
+static lbm_status slot_cells(lbm_solver* s, std::vector<int>& cell) {
+    cell.resize((size_t)held_cells(s));
+    CK(s, cudaMemcpy(cell.data(), s->cellidx, cell.size() * sizeof(int), cudaMemcpyDeviceToHost), "slot map download");
+    return LBM_OK;
+}
+
 lbm_status lbm_set_tau(lbm_solver* s, const double* tau) {
     lbm_status v = enter(s);
     if (v != LBM_OK) return v;
     if (!s->tau) return fail(LBM_EINVAL, "the IR model has no relaxation-time field");
     if (!tau) return fail(LBM_EINVAL, "tau is NULL");
     WAIT(s, "tau transfer");
+    const int n = held_cells(s);
+    std::vector<int> cell;
+    if (s->rank && (v = slot_cells(s, cell)) != LBM_OK) return v;
+    auto at = [&](int k) { return tau[s->rank ? cell[k] : k]; };
     if (arith_bytes(s->p.storage) == 8) {
-        CK(s, cudaMemcpy(s->tau, tau, (size_t)s->ncells * sizeof(double), cudaMemcpyHostToDevice), "tau upload");
+        std::vector<double> t(n);
+        for (int k = 0; k < n; ++k) t[k] = at(k);
+        CK(s, cudaMemcpy(s->tau, t.data(), (size_t)n * sizeof(double), cudaMemcpyHostToDevice), "tau upload");
     } else {
-        std::vector<float> t(s->ncells);
-        for (int i = 0; i < s->ncells; ++i) t[i] = (float)tau[i];
-        CK(s, cudaMemcpy(s->tau, t.data(), (size_t)s->ncells * sizeof(float), cudaMemcpyHostToDevice), "tau upload");
+        std::vector<float> t(n);
+        for (int k = 0; k < n; ++k) t[k] = (float)at(k);
+        CK(s, cudaMemcpy(s->tau, t.data(), (size_t)n * sizeof(float), cudaMemcpyHostToDevice), "tau upload");
     }
     return LBM_OK;
 }
@@ -920,12 +993,24 @@ lbm_status lbm_get_tau(lbm_solver* s, double* tau) {
     if (!s->tau) return fail(LBM_EINVAL, "the IR model has no relaxation-time field");
     if (!tau) return fail(LBM_EINVAL, "tau is NULL");
     WAIT(s, "tau transfer");
+    const int n = held_cells(s);
+    std::vector<int> cell;
+    if (s->rank) {
+        if ((v = slot_cells(s, cell)) != LBM_OK) return v;
+        // solid cells hold no tau in the compact layout: the initial value
+        const double nu0 = s->p.mu_p + s->p.m * s->p.sigma_y;
+        const double t0 = arith_bytes(s->p.storage) == 8 ? 0.5 + 3.0 * nu0 : (double)(float)(0.5 + 3.0 * nu0);
+        for (int i = 0; i < s->ncells; ++i) tau[i] = t0;
+    }
+    auto put = [&](int k, double t) { tau[s->rank ? cell[k] : k] = t; };
     if (arith_bytes(s->p.storage) == 8) {
-        CK(s, cudaMemcpy(tau, s->tau, (size_t)s->ncells * sizeof(double), cudaMemcpyDeviceToHost), "tau download");
+        std::vector<double> t(n);
+        CK(s, cudaMemcpy(t.data(), s->tau, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost), "tau download");
+        for (int k = 0; k < n; ++k) put(k, t[k]);
     } else {
-        std::vector<float> t(s->ncells);
-        CK(s, cudaMemcpy(t.data(), s->tau, (size_t)s->ncells * sizeof(float), cudaMemcpyDeviceToHost), "tau download");
-        for (int i = 0; i < s->ncells; ++i) tau[i] = t[i];
+        std::vector<float> t(n);
+        CK(s, cudaMemcpy(t.data(), s->tau, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost), "tau download");
+        for (int k = 0; k < n; ++k) put(k, t[k]);
     }
     return LBM_OK;
 }
@@ -1075,7 +1160,7 @@ lbm_status lbm_flowrate_noalloc(lbm_solver* s, int axis, double* q_device) {
     if (axis < 0 || axis > 2) return fail(LBM_EINVAL, "axis must be 0, 1 or 2");
     if (!q_device) return fail(LBM_EINVAL, "q_device is NULL");
     if (((uintptr_t)q_device & 7u) != 0) return fail(LBM_EINVAL, "q_device must be 8-byte aligned");
-    const int nb = reduce_grid(s->ncells);
+    const int nb = reduce_grid(held_cells(s));
     if (nb > kStaticParts)
         return fail(LBM_EINVAL, "reduction needs %d partial blocks, the static scratch holds %d",
                     nb, kStaticParts);
@@ -1084,10 +1169,10 @@ lbm_status lbm_flowrate_noalloc(lbm_solver* s, int axis, double* q_device) {
     const void* f = s->f[s->cur];
     cudaError_t e;
     switch (s->lat) {
-    case LBM_D2Q9: e = launch_reduce_D2Q9(s->p.storage, kReduceFlow, s->kp, f, s->links, parts, nb, s->stream); break;
-    case LBM_D3Q15: e = launch_reduce_D3Q15(s->p.storage, kReduceFlow, s->kp, f, s->links, parts, nb, s->stream); break;
-    case LBM_D3Q19: e = launch_reduce_D3Q19(s->p.storage, kReduceFlow, s->kp, f, s->links, parts, nb, s->stream); break;
-    default: e = launch_reduce_D3Q27(s->p.storage, kReduceFlow, s->kp, f, s->links, parts, nb, s->stream); break;
+    case LBM_D2Q9: e = launch_reduce_D2Q9(s->p.storage, kReduceFlow, s->kp, f, s->links, s->cellidx, s->rank, parts, nb, s->stream); break;
+    case LBM_D3Q15: e = launch_reduce_D3Q15(s->p.storage, kReduceFlow, s->kp, f, s->links, s->cellidx, s->rank, parts, nb, s->stream); break;
+    case LBM_D3Q19: e = launch_reduce_D3Q19(s->p.storage, kReduceFlow, s->kp, f, s->links, s->cellidx, s->rank, parts, nb, s->stream); break;
+    default: e = launch_reduce_D3Q27(s->p.storage, kReduceFlow, s->kp, f, s->links, s->cellidx, s->rank, parts, nb, s->stream); break;
     }
     CK(s, e, "static-scratch reduction kernel");
     const int L = axis == 0 ? s->nx : (axis == 1 ? s->ny : s->nz);

@@ -483,6 +483,8 @@ lbm_status lbm_batch_add(lbm_batch* b, lbm_lattice lat, int nx, int ny, int nz,
     lbm_status v = benter(b);
     if (v != LBM_OK) return v;
     if (!p || !id) return fail(LBM_EINVAL, "NULL argument");
+    if (p->flags & LBM_FLAG_COMPACT)
+        return fail(LBM_EINVAL, "batch domains use the dense layout (LBM_FLAG_COMPACT set)");
     if (b->free_slots.empty()) return fail(LBM_EBUSY, "the batch holds %d domains already", kMaxSlots);
     lbm_params q = *p;
     q.check_every = b->k;

@@ -33,6 +33,7 @@ struct KParams {
     int newton;           // PR: Newton iterations of the implicit tau update (0 = explicit)
     uint32_t hash_offset; // added to the cell index in the stochastic-rounding hash
     int cell_begin, cell_end; // cells the single-domain step kernel covers (0, ncells)
+    int nslots;           // compact layout: fluid cells held (0: dense layout)
     FastDiv div_nx, div_ny;   // idx -> (x, y, z) without integer division
 };
 
@@ -56,7 +57,9 @@ struct StepArgs {
     int parity;          // which of the two counters this launch reads
     int block;           // threads per block of plain steps (128, 256 or 512)
     int cpt;             // cells per thread of plain steps (1, or 2 with block 128 / 256)
-    int copy;            // 16-bit PR: solid cells of mixed warps copy through (geometry choice)
+    int copy;            // 16-bit PR: solid cells of mixed groups copy through (geometry choice)
+    const int* cellidx;  // compact layout: cell index of each slot (nullptr: dense layout)
+    const int* rank;     // compact layout: slot of each cell, -1 for solid cells
 };
 
 enum ReduceMode { kReduceFlow = 0, kReduceTotals = 1 };
@@ -68,18 +71,19 @@ struct BatchDesc;   // per-domain descriptor of a batched launch (kernels.cuh)
     cudaError_t launch_step_##L(int model, int storage, bool check, const KParams& kp,          \
                                 const StepArgs& a, cudaStream_t st);                            \
     cudaError_t launch_links_##L(const KParams& kp, const uint8_t* mask, uint32_t* links,       \
-                                 cudaStream_t st);                                              \
+                                 const int* cellidx, cudaStream_t st);                          \
     cudaError_t launch_fields_##L(int storage, const KParams& kp, const void* f,                \
-                                  const uint32_t* links, double* rho, double* ux, double* uy,   \
-                                  double* uz, cudaStream_t st);                                 \
+                                  const uint32_t* links, const int* rank, double* rho,          \
+                                  double* ux, double* uy, double* uz, cudaStream_t st);         \
     cudaError_t launch_reduce_##L(int storage, int mode, const KParams& kp, const void* f,      \
-                                  const uint32_t* links, double* partials, int nblocks,         \
-                                  cudaStream_t st);                                             \
+                                  const uint32_t* links, const int* cellidx, const int* rank,   \
+                                  double* partials, int nblocks, cudaStream_t st);              \
     cudaError_t launch_convert_##L(int storage, bool to_device, const KParams& kp, int q,       \
-                                   void* f, double* plane_buf, cudaStream_t st);                \
+                                   void* f, double* plane_buf, const int* rank, cudaStream_t st);\
     void lattice_table_##L(int* c, double* w);                                                  \
     cudaError_t launch_gather_##L(int storage, const KParams& kp, const void* f,               \
-                                  const int64_t* cells, int n, double* out, cudaStream_t st);   \
+                                  const int64_t* cells, int n, double* out, const int* rank,    \
+                                  cudaStream_t st);                                             \
     cudaError_t launch_halo_##L(int storage, const KParams& kp, void* f, void* buf, int side,   \
                                 bool pack, cudaStream_t st);                                    \
     int face_count_##L();                                                                       \

@@ -16,6 +16,7 @@ namespace blbm {
 struct Layout {
     int64_t plane;
     size_t off_f[2], off_links, off_tau, off_usnap, off_partials, off_stats, off_mask, total;
+    size_t off_cellidx, off_rank;   // compact layout only
     int nparts;
 };
 
@@ -46,7 +47,9 @@ struct lbm_solver {
     bool owns = false;
     char* base = nullptr;
     void* f[2] = {nullptr, nullptr};   // population buffers; f[cur] is the state
-    uint32_t* links = nullptr;
+    uint32_t* links = nullptr;         // per cell, or per slot in the compact layout
+    int* cellidx = nullptr;            // compact layout: cell index of each slot
+    int* rank = nullptr;               // compact layout: slot of each cell (-1: solid)
     void* tau = nullptr;
     void* usnap = nullptr;
     double* partials = nullptr;

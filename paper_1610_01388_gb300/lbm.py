@@ -28,6 +28,7 @@ LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ENONFINITE, LBM_ETIMEOUT, LBM_EBU
     LBM_EUNSUPPORTED = range(8)
 LBM_FLAG_BURNETT_X = 0x1
 LBM_FLAG_Z_GHOSTS = 0x2
+LBM_FLAG_COMPACT = 0x4
 
 LATTICES = {"D2Q9": LBM_D2Q9, "D3Q15": LBM_D3Q15, "D3Q19": LBM_D3Q19, "D3Q27": LBM_D3Q27}
 MODELS = {"PR": LBM_MODEL_PR, "IR": LBM_MODEL_IR}
@@ -47,7 +48,8 @@ EXPORTED = ["lbm_params_default", "lbm_lattice_info", "lbm_workspace_bytes", "lb
             "lbm_tuning_set_batch_concurrency", "lbm_tuning_get_batch_concurrency",
             "lbm_tuning_set_batch_tile", "lbm_tuning_get_batch_tile",
             "lbm_halo_bytes", "lbm_halo_pack", "lbm_halo_unpack", "lbm_set_hash_offset",
-            "lbm_check_sums", "lbm_step_cells", "lbm_step_commit"]
+            "lbm_check_sums", "lbm_step_cells", "lbm_step_commit",
+            "lbm_workspace_bytes_for_mask"]
 LBM_REQ_QUEUED, LBM_REQ_RUNNING, LBM_REQ_CONVERGED, LBM_REQ_CAPPED, LBM_REQ_FAILED = range(5)
 LBM_STEADY_FLOW, LBM_STEADY_RESIDUAL = 0, 1
 
@@ -118,6 +120,7 @@ def library():
             "lbm_params_default": [P(lbm_params)],
             "lbm_lattice_info": [i32, P(i32), P(i32), vp, vp],
             "lbm_workspace_bytes": [i32, i32, i32, i32, P(lbm_params), P(sz)],
+            "lbm_workspace_bytes_for_mask": [i32, i32, i32, i32, vp, P(lbm_params), P(sz)],
             "lbm_create": [P(vp), i32, i32, i32, i32, vp, P(lbm_params), vp],
             "lbm_create_with_workspace": [P(vp), i32, i32, i32, i32, vp, P(lbm_params), vp, vp, sz],
             "lbm_step": [vp, i64],
@@ -229,6 +232,18 @@ def lbm_workspace_bytes(lat, nx, ny, nz, params) -> int:
     b = ctypes.c_size_t()
     _check(library().lbm_workspace_bytes(_lat(lat), nx, ny, nz, ctypes.byref(params),
                                          ctypes.byref(b)))
+    return b.value
+
+
+def lbm_workspace_bytes_for_mask(lat, mask, params) -> int:
+    """mask: uint8 (nz, ny, nx) or (ny, nx)."""
+    mask = np.ascontiguousarray(mask, np.uint8)
+    if mask.ndim == 2:
+        mask = mask[None]
+    nz, ny, nx = mask.shape
+    b = ctypes.c_size_t()
+    _check(library().lbm_workspace_bytes_for_mask(_lat(lat), nx, ny, nz, _ptr(mask),
+                                                  ctypes.byref(params), ctypes.byref(b)))
     return b.value
 
 
@@ -479,7 +494,13 @@ class Solver:
 
     def __init__(self, lattice, mask, model="IR", storage="F32", mu_p=0.1, sigma_y=0.0, m=0.0,
                  gammadot_c=1e-8, g=(0.0, 0.0, 0.0), magic=0.25, check_every=0, flags=0,
-                 newton_iters=0, use_torch=False, stream=None):
+                 newton_iters=0, use_torch=False, stream=None, layout="dense"):
+        """layout: "dense" (every cell held) or "compact" (fluid cells only,
+        LBM_FLAG_COMPACT)."""
+        if layout not in ("dense", "compact"):
+            raise ValueError(f"layout must be 'dense' or 'compact' (got {layout!r})")
+        if layout == "compact":
+            flags |= LBM_FLAG_COMPACT
         self.lattice = lattice
         self.params = lbm_params_default(model=model, storage=storage, mu_p=mu_p,
                                          sigma_y=sigma_y, m=m, gammadot_c=gammadot_c, g=g,
@@ -493,8 +514,7 @@ class Solver:
         ws = None
         if use_torch:
             import torch
-            nz, ny, nx = mask.shape
-            nb = lbm_workspace_bytes(lattice, nx, ny, nz, self.params)
+            nb = lbm_workspace_bytes_for_mask(lattice, mask, self.params)
             self._ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
             ws = (self._ws.data_ptr(), nb)
             if stream is None:

@@ -8,8 +8,8 @@ FP32 or FP64 storage (one value per cell and plane):
 * reads: per plane j, the sectors holding the values pulled from it (a fluid
   cell's fluid neighbour at x - c_j; the cell itself when the neighbour in
   direction opp(j) is solid, the halfway bounce-back), plus, with the
-  copy-through, the own values of the solid cells in warps that hold fluid
-  cells;
+  copy-through, the own values of the solid cells in aligned groups of 8
+  consecutive cells that hold fluid cells (the kernels' copy rule);
 * fills: per plane, the written sectors that the stores cover only in part
   (such a sector is read before it is written);
 * writes: per plane, every sector a store touches;
@@ -17,7 +17,8 @@ FP32 or FP64 storage (one value per cell and plane):
 
 Each sector is counted once per launch (L2 catches the reuse between
 neighbouring warps).  On a 160^3 D3Q27 porous box the total matched an ncu
-capture of the FP32 IR step to 1 %.
+capture of the FP32 IR step to 1 % (copy groups of 32 cells, the kernels'
+rule at the time).
 """
 from __future__ import annotations
 
@@ -29,11 +30,12 @@ SECTOR = 32
 
 
 def sector_traffic(mask: np.ndarray, lattice: str, value_bytes: int = 4,
-                   copy_through: bool = True, warp: int = 32) -> dict:
+                   copy_through: bool = True, group: int = 8) -> dict:
     """Bytes one step moves on `mask` ((nz, ny, nx) or (ny, nx), 1 = solid,
     periodic), split into reads, fills, writes and link words, next to the
     algorithmic bytes (fluid cells x (2 Q value_bytes + 1)).  Populations
-    only: the PR tau field and the check-step snapshot are not counted."""
+    only: the PR tau field and the check-step snapshot are not counted.
+    `group`: cells per copy-through group (8 in the kernels)."""
     if value_bytes not in (4, 8):
         raise ValueError("value_bytes must be 4 (FP32) or 8 (FP64)")
     m = np.asarray(mask)
@@ -56,8 +58,8 @@ def sector_traffic(mask: np.ndarray, lattice: str, value_bytes: int = 4,
     src = [((x - c[i, 0]) % nx) + nx * (((y - c[i, 1]) % ny) + ny * ((z - c[i, 2]) % nz))
            for i in range(q)]
     per = SECTOR // value_bytes
-    warp_has_fluid = np.bincount(idx // warp, weights=fluid.astype(np.int64)) > 0
-    copy = solid & warp_has_fluid[idx // warp] if copy_through else np.zeros(n, bool)
+    group_has_fluid = np.bincount(idx // group, weights=fluid.astype(np.int64)) > 0
+    copy = solid & group_has_fluid[idx // group] if copy_through else np.zeros(n, bool)
     writers = fluid | copy
     cnt = np.bincount(idx[writers] // per, minlength=(n + per - 1) // per)
     touched = int((cnt > 0).sum())

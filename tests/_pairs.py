@@ -33,13 +33,13 @@ def oracle_to_gpu(lat, f_orc):
 
 def make_pair(lat, mask, model="IR", storage="F32", nu_p=0.1, sigma_y=0.0, m=0.0, g=(0, 0, 0),
               magic=0.25, gammadot_c=1e-8, check_every=0, flags=0, use_torch=False, nthreads=0,
-              newton=0):
+              newton=0, layout="dense"):
     mask = np.ascontiguousarray(mask, np.uint8)
     if mask.ndim == 2:
         mask = mask[None]
     s = lbm.Solver(lat, mask, model=model, storage=storage, mu_p=nu_p, sigma_y=sigma_y, m=m,
                    gammadot_c=gammadot_c, g=g, magic=magic, check_every=check_every,
-                   flags=flags, newton_iters=newton, use_torch=use_torch)
+                   flags=flags, newton_iters=newton, use_torch=use_torch, layout=layout)
     p = oracle.params(model=model, nu_p=nu_p, sigma_y=sigma_y, m=m, gdot_c=gammadot_c, g=g,
                       magic=magic, burnett_x=bool(flags & lbm.LBM_FLAG_BURNETT_X), newton=newton)
     o = oracle.State(lat, p, mask, nthreads=nthreads)

@@ -102,6 +102,9 @@ def _create_status(lat, mask, **kw):
     # ghost planes are not stepped: a slab whose interior is all solid has no fluid
     ("D3Q19", np.concatenate([np.zeros((1, 2, 2)), np.ones((1, 2, 2)), np.zeros((1, 2, 2))]),
      {"flags": 0x2}, "no fluid"),
+    # the compact layout holds no ghost planes
+    ("D3Q19", np.zeros((4, 2, 2)), {"flags": 0x2 | 0x4}, "dense layout"),
+    ("D3Q19", np.ones((2, 2, 2)), {"flags": 0x4}, "no fluid"),
 ])
 def test_create_rejects_invalid_arguments(lat, mask, kw, expect):
     st, msg = _create_status(lat, mask, **kw)
@@ -143,6 +146,31 @@ def test_workspace_bytes_cover_the_layout():
     assert n >= 2 * 27 * 4 * cells + 4 * cells + 4 * cells + 12 * cells + cells
     p64 = lbm.lbm_params_default(model="IR", storage="F64")
     assert lbm.lbm_workspace_bytes("D3Q27", 256, 128, 128, p64) >= 2 * 27 * 8 * cells
+
+
+def test_workspace_bytes_for_mask_size_the_compact_layout():
+    """The mask-aware size is exact: equal to the maskless one for the dense
+    layout, and for the compact one the fluid cells' planes plus the two slot
+    maps (cell index per slot, slot per cell), below the maskless bound."""
+    mask = np.ones((16, 16, 64), np.uint8)
+    mask[:, :, :16] = 0                                # 4096 fluid cells of 16384
+    for model in ("PR", "IR"):
+        for storage in ("F32", "F16", "F64"):
+            d = lbm.lbm_params_default(model=model, storage=storage, check_every=10)
+            c = lbm.lbm_params_default(model=model, storage=storage, check_every=10,
+                                       flags=lbm.LBM_FLAG_COMPACT)
+            dense = lbm.lbm_workspace_bytes_for_mask("D3Q19", mask, d)
+            assert dense == lbm.lbm_workspace_bytes("D3Q19", 64, 16, 16, d)
+            comp = lbm.lbm_workspace_bytes_for_mask("D3Q19", mask, c)
+            bound = lbm.lbm_workspace_bytes("D3Q19", 64, 16, 16, c)
+            sb = {"F32": 4, "F16": 2, "F64": 8}[storage]
+            rs = 8 if storage == "F64" else 4
+            per_slot = 2 * 19 * sb + 4 + 4 + 3 * rs + (rs if model == "PR" else 0)
+            assert comp >= 4096 * per_slot + 16384 * (1 + 4)
+            assert comp < dense < bound
+    with pytest.raises(lbm.LbmError):
+        lbm.lbm_workspace_bytes_for_mask("D3Q19", np.ones((2, 2, 2), np.uint8),
+                                         lbm.lbm_params_default())
 
 
 def test_tuning_table_host_logic():

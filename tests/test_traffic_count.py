@@ -45,6 +45,18 @@ def test_one_solid_cell_costs_one_fill_per_plane(fp64):
     assert rc["fills"] == 0 and rc["writes"] == r["writes"]
 
 
+def test_copy_through_moves_only_groups_with_fluid():
+    """One fluid cell in a row of 32 solid ones: its group of 8 cells is one
+    sector per plane, copied through whole; the other three groups of the
+    warp are not touched.  Counting by warps of 32 would move all four."""
+    m = np.ones((3, 3, 32), np.uint8)
+    m[1, 1, 11] = 0
+    r = traffic.sector_traffic(m, "D3Q19")
+    assert r["fills"] == 0 and r["writes"] == 19 * 32
+    rw = traffic.sector_traffic(m, "D3Q19", group=32)
+    assert rw["fills"] == 0 and rw["writes"] == 4 * 19 * 32
+
+
 def test_copy_through_leaves_no_partial_sector_and_skips_solid_warps():
     m, _ = W.porous_mask(32, porosity=0.7, r_min=3.0, r_max=5.0, seed=4)
     r0 = traffic.sector_traffic(m, "D3Q19", copy_through=False)
