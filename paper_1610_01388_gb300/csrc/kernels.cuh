@@ -1136,24 +1136,39 @@ __device__ __forceinline__ void compact_cell(const KParams& kp, const Coef<typen
 template <class L, int MODEL, class S, bool CHECK> constexpr int compact_min_blocks() {
     if (std::is_same<typename Store<S>::R, double>::value) return 0;
     if (BLBM_COMPACT_MINB >= 0) return BLBM_COMPACT_MINB;
-    // IR: 6 blocks of 256 (40 registers, no spill): on the 256^3 porous box
-    // 378 -> 361 us (FP32) and 318 -> 302 us (FP16) against the allocator's
-    // 38 registers; PR keeps the dense step's budget (6 blocks spilled and
-    // made the FP16 step 7 % slower)
-    if (MODEL == LBM_MODEL_IR && !CHECK) return 6;
+    // IR up to 19 velocities: 6 blocks of 256 (40 registers): on the 256^3
+    // porous box, D3Q19, 378 -> 361 us (FP32) and 318 -> 302 us (FP16) against
+    // the allocator's 38 registers (D3Q27 spills at that budget and is left to
+    // the allocator, as in the dense step).  PR keeps the dense step's budget
+    // (6 blocks spilled and made the FP16 step 7 % slower).
+    if (MODEL == LBM_MODEL_IR && !CHECK && L::Q <= 19) return 6;
     return step_min_blocks<L, MODEL, S, CHECK, kBlock>();
 }
 
-template <class L, int MODEL, class S, bool CHECK>
-__global__ void __launch_bounds__(kBlock, compact_min_blocks<L, MODEL, S, CHECK>())
+// Threads per block of the plain compact step (check steps: kBlock).  A
+// block's rank words come from the rows next to its cells, so a wider block
+// reuses more of them from L1; the register budget per SM stays the same.
+// 256^3 porous box, D3Q19: IR (FP32) 373 / 361 / 349 us at 128 / 256 / 512
+// threads; PR, whose budget at 512 threads loses occupancy, 400 / 405 / 500
+// (FP32) and 331 / 338 / 406 (FP16).  BLBM_COMPACT_BLOCK overrides it.
+#ifndef BLBM_COMPACT_BLOCK
+#define BLBM_COMPACT_BLOCK 0
+#endif
+template <int MODEL> constexpr int compact_block() {
+    return BLBM_COMPACT_BLOCK > 0 ? BLBM_COMPACT_BLOCK : (MODEL == LBM_MODEL_IR ? 512 : 128);
+}
+
+template <class L, int MODEL, class S, bool CHECK, int BLOCK = kBlock>
+__global__ void __launch_bounds__(BLOCK, compact_min_blocks<L, MODEL, S, CHECK>() * kBlock / BLOCK)
 k_step_compact(const KArgs a, const SrcPlanes<S> src, const DstPlanes<S> dst,
                const uint32_t* __restrict__ links, const int* __restrict__ cellidx,
                const int* __restrict__ rank, typename Store<S>::R* __restrict__ tau,
                typename Store<S>::R* __restrict__ usnap, double* __restrict__ partials,
                uint32_t* __restrict__ rng_ctr, int parity) {
+    static_assert(!CHECK || BLOCK == kBlock, "check steps use the fixed block size");
     using R = typename Store<S>::R;
     const KParams& kp = a.kp;
-    const int slot = blockIdx.x * kBlock + threadIdx.x;
+    const int slot = blockIdx.x * BLOCK + threadIdx.x;
     uint32_t seed = 0u;
     if constexpr (Store<S>::kStochastic) {
         // this launch reads counter[parity] and leaves counter + 1 for the next
@@ -1761,7 +1776,8 @@ cudaError_t launch_step_compact(bool check, const KParams& kp, const StepArgs& s
         k_step_compact_loop<L, MODEL, S><<<pgrid, kBlock, 0, st>>>(
             a, src, dst, s.links, s.cellidx, s.rank, (R*)s.tau, s.rng_ctr, s.parity);
     } else {
-        k_step_compact<L, MODEL, S, false><<<grid, kBlock, 0, st>>>(
+        constexpr int B = compact_block<MODEL>();
+        k_step_compact<L, MODEL, S, false, B><<<(kp.nslots + B - 1) / B, B, 0, st>>>(
             a, src, dst, s.links, s.cellidx, s.rank, (R*)s.tau, (R*)s.usnap, s.partials,
             s.rng_ctr, s.parity);
     }
