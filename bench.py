@@ -111,14 +111,19 @@ def workload_mask(nx=None):
 # layout, storage and model.  Both are valid only
 # for the device-code sources they were captured with (KERNEL_FINGERPRINT)
 # and are reported as null once any of those sources changes.
-NCU_TRAFFIC_POROUS = {}
-NCU_TRAFFIC = {
-    ("F32", "IR", 128, 1): 855828959, ("F32", "IR", 128, 2): 855420895, ("F32", "IR", 256, 1): 855586898, ("F32", "IR", 256, 2): 857031687, ("F32", "IR", 512, 1): 857374821,
-    ("F32", "PR", 128, 1): 889919270, ("F32", "PR", 128, 2): 889816892, ("F32", "PR", 256, 1): 889681265, ("F32", "PR", 256, 2): 890840825, ("F32", "PR", 512, 1): 890229380,
-    ("F16", "IR", 128, 1): 419953085, ("F16", "IR", 128, 2): 419266469, ("F16", "IR", 256, 1): 419741658, ("F16", "IR", 256, 2): 420161778, ("F16", "IR", 512, 1): 420531845,
-    ("F16", "PR", 128, 1): 451661161, ("F16", "PR", 128, 2): 450987730, ("F16", "PR", 256, 1): 451111067, ("F16", "PR", 256, 2): 451170799, ("F16", "PR", 512, 1): 451244961,
+NCU_TRAFFIC_POROUS = {
+    ('compact', 'F16', 'IR'): 1019034835, ('compact', 'F16', 'PR'): 1112421450,
+    ('compact', 'F32', 'IR'): 1911234658, ('compact', 'F32', 'PR'): 1998262731,
+    ('dense', 'F16', 'IR'): 1249617661, ('dense', 'F16', 'PR'): 1377772508,
+    ('dense', 'F32', 'IR'): 2433567378, ('dense', 'F32', 'PR'): 2559409054,
 }
-KERNEL_FINGERPRINT = "a24c4b9b1664c0d1"
+NCU_TRAFFIC = {
+    ('F16', 'IR', 128, 1): 420067060, ('F16', 'IR', 128, 2): 419211478, ('F16', 'IR', 256, 1): 419798816, ('F16', 'IR', 256, 2): 420116716, ('F16', 'IR', 512, 1): 420233243,
+    ('F16', 'PR', 128, 1): 451343989, ('F16', 'PR', 128, 2): 450980370, ('F16', 'PR', 256, 1): 451374730, ('F16', 'PR', 256, 2): 451160087, ('F16', 'PR', 512, 1): 451244054,
+    ('F32', 'IR', 128, 1): 855902677, ('F32', 'IR', 128, 2): 855409884, ('F32', 'IR', 256, 1): 855634397, ('F32', 'IR', 256, 2): 857033274, ('F32', 'IR', 512, 1): 857491647,
+    ('F32', 'PR', 128, 1): 889853742, ('F32', 'PR', 128, 2): 889944522, ('F32', 'PR', 256, 1): 889648778, ('F32', 'PR', 256, 2): 890834590, ('F32', 'PR', 512, 1): 890219245,
+}
+KERNEL_FINGERPRINT = "ef33bf07e12c43a7"
 KERNEL_SOURCES = ("kernels.cuh", "lattice.cuh", "lbm_internal.h", "fastdiv.h", "kern_d3q27.cu",
                   "kern_d3q19.cu")
 
