@@ -19,29 +19,32 @@ from paper_1610_01388_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 
-def _solver(lat, mask, model, storage="F32"):
+def _solver(lat, mask, model, storage="F32", layout="dense"):
     g = (2e-5, -4e-6, 0.0 if lat == "D2Q9" else 3e-6)
     return lbm.Solver(lat, mask, model=model, storage=storage, mu_p=0.08, sigma_y=1e-5, m=1e5,
-                      g=g)
+                      g=g, layout=layout)
 
 
 # The reduction runs at most 1216 blocks of 256 cells and strides over the
 # rest, so domains above 311,296 cells (the bench duct, the porous box) take
 # the grid-stride loop and fill every partial of the static array.
-@pytest.mark.parametrize("lat,shape,model,storage", [
-    ("D3Q19", (13, 17, 40), "IR", "F32"),
-    ("D3Q27", (9, 11, 300), "PR", "F32"),
-    ("D2Q9", (1, 64, 4), "IR", "F32"),
-    ("D3Q27", (128, 128, 256), "PR", "F32"),
-    ("D3Q19", (96, 96, 96), "IR", "F16"),
+# (compact layout: the reduction strides over the fluid slots; 96^3 holds
+# 875,520 of them)
+@pytest.mark.parametrize("lat,shape,model,storage,layout", [
+    ("D3Q19", (13, 17, 40), "IR", "F32", "dense"),
+    ("D3Q27", (9, 11, 300), "PR", "F32", "dense"),
+    ("D2Q9", (1, 64, 4), "IR", "F32", "dense"),
+    ("D3Q27", (128, 128, 256), "PR", "F32", "dense"),
+    ("D3Q19", (96, 96, 96), "IR", "F16", "dense"),
+    ("D3Q19", (96, 96, 96), "PR", "F32", "compact"),
 ])
-def test_noalloc_flowrate_matches_flowrate_on_two_calls(lat, shape, model, storage):
+def test_noalloc_flowrate_matches_flowrate_on_two_calls(lat, shape, model, storage, layout):
     import torch
     mask = np.zeros(shape, np.uint8)
     mask[:, 0, :] = 1
     if shape[0] > 1:
         mask[0, :, :] = 1
-    s = _solver(lat, mask, model, storage)
+    s = _solver(lat, mask, model, storage, layout)
     q_dev = torch.zeros(4, dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
     for call, steps in enumerate((37, 64)):
