@@ -20,7 +20,8 @@ larger than L2, so no flush is needed between steps.
 
 Also reported, outside the timed region: the porous box of the porous-medium
 workload (256^3, D3Q19, FP32 and FP16 storage, both models) with its own
-roofline, the precision workload's 512x192x192 duct (FP32 and FP16), the
+roofline, the precision workload's 512x192x192 duct and 512^3 porous box
+(D3Q27, FP32 and FP16; the box in the compact layout), the
 same metric end to end through the C ABI with host buffers, and the
 continuous-batching server on a Poisson stream of independent solves run to
 steady state.
@@ -515,10 +516,78 @@ def run_precision_record(args):
     for model in ("IR", "PR"):
         a, r = u_of[("F16", model)][:, fl], u_of[("F32", model)][:, fl]
         diff[model] = float(np.linalg.norm(a - r) / np.linalg.norm(r))
-    return {"workload": f"square duct D3Q27 {nx}x{ny}x{nz} ({ny - 1}x{nz - 1} fluid), Bn={BN:g}, "
-                        f"nu_p={NU_P}, PR m={M_PR:g}, from rest",
-            "fluid_cells": nfluid, "lattice_steps": n, "peak_gbs": peak,
-            "peak_kind": f"{kind} (copy bandwidth)", "kernels": out,
+    rec = {"workload": f"square duct D3Q27 {nx}x{ny}x{nz} ({ny - 1}x{nz - 1} fluid), Bn={BN:g}, "
+                       f"nu_p={NU_P}, PR m={M_PR:g}, from rest",
+           "fluid_cells": nfluid, "lattice_steps": n, "peak_gbs": peak,
+           "peak_kind": f"{kind} (copy bandwidth)", "kernels": out,
+           "rel_l2_u_f16_vs_f32_at_equal_steps": diff}
+    if args.precision_porous > 0:
+        rec["porous"] = run_precision_porous(args)
+    return rec
+
+
+PRECISION_POROUS_BN = 0.5
+
+
+def run_precision_porous(args):
+    """The precision workload's porous box: args.precision_porous^3 cells of
+    random non-overlapping spheres (radius 6-10, target porosity 0.6, seed 1;
+    random sequential addition jams above it, so the packing stops after
+    2e6 candidates, near porosity 0.67), D3Q27, both models, FP32 and FP16
+    offset storage in the compact layout, timed as the duct is.  Bn = 0.5 a
+    priori: at the porous record's Bn = 2 this box is near-jammed, where FP16
+    storage does not resolve the flow.  The FP16 velocity field is compared
+    with the FP32 one at the same step count on the device."""
+    import torch
+    from paper_1610_01388_gb300 import lbm
+    from paper_1610_01388_gb300 import workloads as W
+    side = args.precision_porous
+    mask, info = W.porous_mask(side, porosity=0.6, r_min=6.0, r_max=10.0, seed=1,
+                               max_attempts=2_000_000)
+    fl = torch.from_numpy(mask.reshape(-1) == 0).cuda()
+    nfluid = int(fl.sum())
+    prm = W.porous_params(nu_p=NU_P, d_mean=16.0, g=2e-5, bn=PRECISION_POROUS_BN)
+    peak, kind = measured_hbm_peak()
+    st = torch.cuda.current_stream()
+    out, diff, u32 = {}, {}, {}
+    for storage in ("F32", "F16"):
+        for model in ("IR", "PR"):
+            s = lbm.Solver("D3Q27", mask, model=model, storage=storage, mu_p=NU_P,
+                           sigma_y=prm["sigma_y"], m=M_PR, g=(prm["g"], 0.0, 0.0),
+                           check_every=CHECK_EVERY, use_torch=True, layout="compact")
+            s.step(CHECK_EVERY)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(st)
+            s.step(args.precision_steps)
+            e1.record(st)
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1) / 1e3 / args.precision_steps
+            b = s.info.bytes_per_fluid_update
+            u = torch.empty((3, mask.size), dtype=torch.float64, device="cuda")
+            lbm.lbm_fields_device(s.h, 0, u[0].data_ptr(), u[1].data_ptr(), u[2].data_ptr())
+            torch.cuda.synchronize()
+            s.close()
+            u = u[:, fl]
+            if storage == "F32":
+                u32[model] = u
+            else:
+                r = u32.pop(model)
+                diff[model] = float(torch.linalg.norm(u - r) / torch.linalg.norm(r))
+            del u
+            gbs = b * nfluid / t / 1e9
+            name = "k_step_compact_loop" if (model == "IR" and storage == "F16") else "k_step_compact"
+            out[f"{model}/{storage}"] = {
+                "kernel": f"{name}<D3Q27,{model},{STORAGE_CTYPE[storage]}>",
+                "launch_us": round(t * 1e6, 2), "mlups": round(nfluid / t / 1e6, 1),
+                "bytes_per_fluid_update": b, "achieved_gbs": round(gbs, 1),
+                "frac": round(gbs / peak, 4)}
+    return {"workload": f"porous box D3Q27 {side}^3 (random non-overlapping spheres, radius "
+                        f"6-10, porosity {info['porosity']:.3f}, seed 1, 2e6 candidates), "
+                        f"Bn={PRECISION_POROUS_BN:g} a priori, nu_p={NU_P}, PR m={M_PR:g}, "
+                        f"compact layout, from rest",
+            "fluid_cells": nfluid, "cells": int(mask.size),
+            "lattice_steps": CHECK_EVERY + args.precision_steps, "kernels": out,
             "rel_l2_u_f16_vs_f32_at_equal_steps": diff}
 
 
@@ -838,6 +907,8 @@ def main(argv=None):
     ap.add_argument("--porous-steps", type=int, default=500)
     ap.add_argument("--precision-steps", type=int, default=500,
                     help="lattice steps timed on the precision workload's duct (0 skips it)")
+    ap.add_argument("--precision-porous", type=int, default=512, metavar="SIDE",
+                    help="side of the precision workload's porous box (0 skips it)")
     ap.add_argument("--serve-storage", default="F16,F32,mixed",
                     help="storage forms served, comma-separated, in order (mixed: FP16, with "
                          "FP32 for the near-jammed porous requests)")

@@ -1138,10 +1138,10 @@ template <class L, int MODEL, class S, bool CHECK> constexpr int compact_min_blo
     if (BLBM_COMPACT_MINB >= 0) return BLBM_COMPACT_MINB;
     // IR up to 19 velocities: 6 blocks of 256 (40 registers): on the 256^3
     // porous box, D3Q19, 378 -> 361 us (FP32) and 318 -> 302 us (FP16) against
-    // the allocator's 38 registers (D3Q27 spills at that budget and is left to
-    // the allocator, as in the dense step).  PR keeps the dense step's budget
-    // (6 blocks spilled and made the FP16 step 7 % slower).
-    if (MODEL == LBM_MODEL_IR && !CHECK && L::Q <= 19) return 6;
+    // the allocator's 38 registers.  D3Q27 IR: 4 blocks (64 registers; 48
+    // spilled and ran slower).  PR keeps the dense step's budget (6 blocks
+    // spilled and made the D3Q19 FP16 step 7 % slower).
+    if (MODEL == LBM_MODEL_IR && !CHECK) return L::Q <= 19 ? 6 : 4;
     return step_min_blocks<L, MODEL, S, CHECK, kBlock>();
 }
 
@@ -1150,12 +1150,16 @@ template <class L, int MODEL, class S, bool CHECK> constexpr int compact_min_blo
 // reuses more of them from L1; the register budget per SM stays the same.
 // 256^3 porous box, D3Q19: IR (FP32) 373 / 361 / 349 us at 128 / 256 / 512
 // threads; PR, whose budget at 512 threads loses occupancy, 400 / 405 / 500
-// (FP32) and 331 / 338 / 406 (FP16).  BLBM_COMPACT_BLOCK overrides it.
+// (FP32) and 331 / 338 / 406 (FP16).  D3Q27 IR, whose 64 registers allow
+// only two blocks of 512 per SM: 581 us at 512 threads, 512 us at 256 (256^3
+// box, porosity 0.7).  BLBM_COMPACT_BLOCK overrides it.
 #ifndef BLBM_COMPACT_BLOCK
 #define BLBM_COMPACT_BLOCK 0
 #endif
-template <int MODEL> constexpr int compact_block() {
-    return BLBM_COMPACT_BLOCK > 0 ? BLBM_COMPACT_BLOCK : (MODEL == LBM_MODEL_IR ? 512 : 128);
+template <class L, int MODEL> constexpr int compact_block() {
+    if (BLBM_COMPACT_BLOCK > 0) return BLBM_COMPACT_BLOCK;
+    if (MODEL != LBM_MODEL_IR) return 128;
+    return L::Q <= 19 ? 512 : 256;
 }
 
 template <class L, int MODEL, class S, bool CHECK, int BLOCK = kBlock>
@@ -1207,8 +1211,10 @@ template <int MODEL, class S> constexpr bool compact_loop() {
 #ifndef BLBM_COMPACT_LOOP_MINB
 #define BLBM_COMPACT_LOOP_MINB -1
 #endif
+// D3Q27: 5 blocks (48 registers): 425 -> 374 us against the allocator's 64.
 template <class L, int MODEL, class S> constexpr int compact_loop_min_blocks() {
     if (BLBM_COMPACT_LOOP_MINB >= 0) return BLBM_COMPACT_LOOP_MINB;
+    if (L::Q == 27) return 5;
     return compact_min_blocks<L, MODEL, S, false>();
 }
 
@@ -1776,7 +1782,7 @@ cudaError_t launch_step_compact(bool check, const KParams& kp, const StepArgs& s
         k_step_compact_loop<L, MODEL, S><<<pgrid, kBlock, 0, st>>>(
             a, src, dst, s.links, s.cellidx, s.rank, (R*)s.tau, s.rng_ctr, s.parity);
     } else {
-        constexpr int B = compact_block<MODEL>();
+        constexpr int B = compact_block<L, MODEL>();
         k_step_compact<L, MODEL, S, false, B><<<(kp.nslots + B - 1) / B, B, 0, st>>>(
             a, src, dst, s.links, s.cellidx, s.rank, (R*)s.tau, (R*)s.usnap, s.partials,
             s.rng_ctr, s.parity);
