@@ -355,6 +355,8 @@ void lbm_destroy(lbm_solver *s);
  * graphs).  Check steps always use 256 threads, so flow rates and residuals
  * do not depend on the tuning.  The project's autotuner
  * (paper_1610_01388_gb300.autotune) measures the candidates and fills it.
+ * It applies to the dense layout; the compact layout's step has fixed
+ * shapes per lattice and model, chosen by measurement on porous boxes. 
  * ------------------------------------------------------------------------ */
 lbm_status lbm_tuning_set(lbm_lattice lat, int32_t model, int32_t storage, int32_t size_class,
                           int32_t block);
@@ -485,7 +487,8 @@ enum { LBM_STEADY_FLOW = 0, LBM_STEADY_RESIDUAL = 1 };
 typedef struct {
     int32_t lattice, nx, ny, nz;
     const uint8_t *solid_mask;  /* host, nx*ny*nz, copied at submit */
-    lbm_params params;
+    lbm_params params;          /* flags: not LBM_FLAG_COMPACT or LBM_FLAG_Z_GHOSTS
+                                   (LBM_EINVAL at submit) */
     double tolerance;           /* steady state: change per check interval < tolerance */
     int64_t max_steps;          /* step cap (> 0) */
     int32_t keep_fields;        /* keep rho and u_real of the final state on the host */

@@ -783,6 +783,9 @@ lbm_status lbm_server_submit(lbm_server* s, const lbm_request* req, int64_t* id)
         return fail(LBM_EINVAL, "unknown steady-state criterion %d", req->criterion);
     if (req->nx < 1 || req->ny < 1 || req->nz < 1 || !req->solid_mask)
         return fail(LBM_EINVAL, "bad extents or mask");
+    if (req->params.flags & (LBM_FLAG_COMPACT | LBM_FLAG_Z_GHOSTS))
+        return fail(LBM_EINVAL, "served domains are whole domains in the dense layout (flags 0x%x)",
+                    req->params.flags);
     lbm_params q = req->params;
     q.check_every = s->k;
     size_t bytes = 0;

@@ -153,7 +153,8 @@ def test_compact_probes_and_uploads():
 
 
 def test_compact_refusals():
-    """Steps in parts need the dense planes; batches take dense domains."""
+    """Steps in parts need the dense planes; batches and the server take
+    whole dense domains."""
     mask = _mask("D3Q19")
     c = lbm.Solver("D3Q19", mask, layout="compact", use_torch=True)
     for call in (lambda: lbm.lbm_step_cells(c.h, 0, 10), lambda: lbm.lbm_step_commit(c.h)):
@@ -166,6 +167,12 @@ def test_compact_refusals():
         b.add("D3Q19", mask, flags=lbm.LBM_FLAG_COMPACT)
     assert e.value.status == lbm.LBM_EINVAL
     b.close()
+    srv = lbm.Server(1 << 30, check_every=10)
+    for flags in (lbm.LBM_FLAG_COMPACT, lbm.LBM_FLAG_Z_GHOSTS):
+        with pytest.raises(lbm.LbmError) as e:
+            srv.submit("D3Q19", mask, flags=flags)
+        assert e.value.status == lbm.LBM_EINVAL
+    srv.close()
 
 
 @pytest.mark.parametrize("storage", ["F16", "BF16"])
