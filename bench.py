@@ -113,18 +113,18 @@ def workload_mask(nx=None):
 # for the device-code sources they were captured with (KERNEL_FINGERPRINT)
 # and are reported as null once any of those sources changes.
 NCU_TRAFFIC_POROUS = {
-    ('compact', 'F16', 'IR'): 1019431948, ('compact', 'F16', 'PR'): 1112484620,
-    ('compact', 'F32', 'IR'): 1911246881, ('compact', 'F32', 'PR'): 1998323291,
-    ('dense', 'F16', 'IR'): 1249646528, ('dense', 'F16', 'PR'): 1377771826,
-    ('dense', 'F32', 'IR'): 2433592346, ('dense', 'F32', 'PR'): 2559473664,
+    ('compact', 'F16', 'IR'): 1017978014, ('compact', 'F16', 'PR'): 1113269616,
+    ('compact', 'F32', 'IR'): 1903769109, ('compact', 'F32', 'PR'): 1998954998,
+    ('dense', 'F16', 'IR'): 1249633474, ('dense', 'F16', 'PR'): 1377774772,
+    ('dense', 'F32', 'IR'): 2433578501, ('dense', 'F32', 'PR'): 2559411298,
 }
 NCU_TRAFFIC = {
-    ('F16', 'IR', 128, 1): 420036636, ('F16', 'IR', 128, 2): 419229556, ('F16', 'IR', 256, 1): 419805405, ('F16', 'IR', 256, 2): 420142044, ('F16', 'IR', 512, 1): 420252292,
-    ('F16', 'PR', 128, 1): 451704945, ('F16', 'PR', 128, 2): 450989143, ('F16', 'PR', 256, 1): 451125185, ('F16', 'PR', 256, 2): 451165995, ('F16', 'PR', 512, 1): 451236234,
-    ('F32', 'IR', 128, 1): 855923388, ('F32', 'IR', 128, 2): 855470531, ('F32', 'IR', 256, 1): 855658340, ('F32', 'IR', 256, 2): 857018120, ('F32', 'IR', 512, 1): 857878868,
-    ('F32', 'PR', 128, 1): 890001312, ('F32', 'PR', 128, 2): 889965624, ('F32', 'PR', 256, 1): 889652453, ('F32', 'PR', 256, 2): 890856198, ('F32', 'PR', 512, 1): 890226671,
+    ('F16', 'IR', 128, 1): 420014114, ('F16', 'IR', 128, 2): 419242511, ('F16', 'IR', 256, 1): 419807719, ('F16', 'IR', 256, 2): 420148489, ('F16', 'IR', 512, 1): 420246713,
+    ('F16', 'PR', 128, 1): 451687740, ('F16', 'PR', 128, 2): 450993049, ('F16', 'PR', 256, 1): 451128599, ('F16', 'PR', 256, 2): 451178877, ('F16', 'PR', 512, 1): 451255470,
+    ('F32', 'IR', 128, 1): 855939396, ('F32', 'IR', 128, 2): 855419924, ('F32', 'IR', 256, 1): 855652990, ('F32', 'IR', 256, 2): 857036609, ('F32', 'IR', 512, 1): 857513376,
+    ('F32', 'PR', 128, 1): 889867913, ('F32', 'PR', 128, 2): 889934811, ('F32', 'PR', 256, 1): 889658765, ('F32', 'PR', 256, 2): 890827582, ('F32', 'PR', 512, 1): 890181304,
 }
-KERNEL_FINGERPRINT = "5fe06df51505220d"
+KERNEL_FINGERPRINT = "49211dcd9ff1d162"
 KERNEL_SOURCES = ("kernels.cuh", "lattice.cuh", "lbm_internal.h", "fastdiv.h", "kern_d3q27.cu",
                   "kern_d3q19.cu")
 
