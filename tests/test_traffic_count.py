@@ -68,3 +68,46 @@ def test_copy_through_leaves_no_partial_sector_and_skips_solid_warps():
     solid_box = np.ones((2, 2, 64), np.uint8)
     rs = traffic.sector_traffic(solid_box, "D3Q19")
     assert rs["reads"] == rs["writes"] == rs["fills"] == 0 and rs["links"] == 4 * 256
+
+
+@pytest.mark.parametrize("lat", ["D2Q9", "D3Q19", "D3Q27"])
+def test_compact_all_fluid_box_adds_only_the_maps(lat):
+    """No solid cell: slots are cells, so the compact layout moves what the
+    dense one does, plus the slot map (4 bytes per cell; its link words
+    replace the dense ones) and the rank words (4 per cell)."""
+    shape = (16, 8) if lat == "D2Q9" else (4, 6, 16)
+    m = np.zeros(shape, np.uint8)
+    n, q = m.size, _q(lat)
+    d = traffic.sector_traffic(m, lat)
+    c = traffic.compact_traffic(m, lat)
+    assert c["reads"] == c["writes"] == q * n * 4
+    assert c["maps"] == 12 * n
+    assert c["total"] == d["total"] + 8 * n
+    # whole 64-byte pairs are read in full: no change
+    assert traffic.compact_traffic(m, lat, read_bytes=64)["total"] == c["total"]
+
+
+def test_compact_single_fluid_cell_reads_only_its_own_slot():
+    """One fluid cell among solid ones: every population but the rest one
+    bounces back, so each plane is read and written at the cell's own slot
+    (one sector each), and no rank word is read."""
+    m = np.ones((3, 3, 32), np.uint8)
+    m[1, 1, 11] = 0
+    c = traffic.compact_traffic(m, "D3Q19")
+    assert c["reads"] == c["writes"] == 19 * 32
+    assert c["maps"] == 2 * 32
+    assert c["algorithmic"] == 2 * 19 * 4 + 1
+
+
+def test_compact_moves_fewer_bytes_than_dense_on_a_porous_box():
+    """Porosity 0.7: the dense layout moves the solid cells that share an
+    access with fluid ones, the compact one only its maps on top of the
+    fluid cells' bytes; 64-byte reads widen the gap."""
+    m, _ = W.porous_mask(32, porosity=0.7, r_min=3.0, r_max=5.0, seed=4)
+    for rb in (32, 64):
+        d = traffic.sector_traffic(m, "D3Q19", read_bytes=rb)
+        c = traffic.compact_traffic(m, "D3Q19", read_bytes=rb)
+        assert c["ratio"] < d["ratio"]
+        assert c["reads"] <= d["reads"] and c["writes"] < d["writes"]
+    assert (traffic.sector_traffic(m, "D3Q19", read_bytes=64)["reads"]
+            >= traffic.sector_traffic(m, "D3Q19")["reads"])
